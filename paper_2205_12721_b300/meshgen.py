@@ -1,0 +1,187 @@
+"""Seeded synthetic meshes: the inputs shared by the CUDA path, the oracle, the
+tests and the benchmark.
+
+This module builds geometry only.  It holds none of the TMOP arithmetic (no
+basis evaluation, Jacobian, metric or quadrature), so both sides of a parity
+test receive identical inputs without sharing any of the method's code.
+
+Meshes are structured Q_p quadrilateral / hexahedral meshes of [0,1]^d
+(paper Sec. 2.1).  Within an element, nodes sit at the tensor product of the
+Gauss-Lobatto-Legendre points of degree p; node and element numbering is
+lexicographic, matching the local ordering of paper Sec. 3.1:
+
+* global node (I_1, .., I_d) -> I_1 + M_1 (I_2 + M_2 I_3), M_k = p n_k + 1;
+* element (e_1, .., e_d) -> e_1 + n_1 (e_2 + n_2 e_3);
+* ``map[e, i]`` = global node of local node i = i_1 + (p+1) i_2 + (p+1)^2 i_3.
+
+Positions are component-major: ``x[a * Nx + node]``.  Boundary nodes of the
+cube are fixed in every component (the fixed-boundary reading of the
+benchmark configurations).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+from numpy.polynomial import legendre as _leg
+
+BASE_SEED = 20260101
+
+
+def gll_points(n: int) -> np.ndarray:
+    """n Gauss-Lobatto-Legendre points on [0,1] (end points plus the roots of
+    P'_{n-1}), from numpy's Legendre-series root finder."""
+    if n < 2:
+        raise ValueError("need at least 2 points")
+    c = np.zeros(n)
+    c[-1] = 1.0
+    inner = np.sort(np.real(_leg.legroots(_leg.legder(c)))) if n > 2 else np.zeros(0)
+    z = np.concatenate([[-1.0], inner, [1.0]])
+    return (z + 1.0) / 2.0
+
+
+@dataclass
+class StructuredMesh:
+    dim: int
+    order: int
+    n: tuple                     # elements per side
+    x: np.ndarray                # (dim * Nx,) float64, component-major
+    map: np.ndarray              # (E, (p+1)^dim) int32
+    fixed: np.ndarray            # (dim * Nx,) uint8
+    grid: tuple = field(default=())   # nodes per side M_k
+
+    @property
+    def num_nodes(self) -> int:
+        return int(np.prod(self.grid))
+
+    @property
+    def num_elems(self) -> int:
+        return int(self.map.shape[0])
+
+    @property
+    def ndof(self) -> int:
+        return self.dim * self.num_nodes
+
+    @property
+    def h(self) -> float:
+        return 1.0 / max(self.n)
+
+    def copy(self) -> "StructuredMesh":
+        return StructuredMesh(self.dim, self.order, self.n, self.x.copy(), self.map, self.fixed,
+                              self.grid)
+
+
+def structured(dim: int, order: int, n_e, ) -> StructuredMesh:
+    """Uniform Cartesian Q_order mesh of [0,1]^dim with n_e elements per side
+    (an int, or one count per axis)."""
+    if dim not in (2, 3) or order < 1:
+        raise ValueError("dim must be 2 or 3 and order >= 1")
+    ns = tuple([int(n_e)] * dim) if np.isscalar(n_e) else tuple(int(v) for v in n_e)
+    ni = order + 1
+    M = tuple(order * n + 1 for n in ns)
+    g = gll_points(ni)
+    coords = []
+    for k in range(dim):
+        c = np.empty(M[k])
+        for e in range(ns[k]):
+            c[order * e: order * e + ni] = (e + g) / ns[k]
+        c[-1] = 1.0
+        coords.append(c)
+    Nx = int(np.prod(M))
+    # node grid (I_1 fastest)
+    idx = np.indices(M[::-1])[::-1]          # idx[k] has shape M reversed, I_k values
+    x = np.empty(dim * Nx)
+    for a in range(dim):
+        x[a * Nx:(a + 1) * Nx] = coords[a][idx[a].reshape(-1)]
+    # element map
+    eidx = np.indices(ns[::-1])[::-1]        # element multi-indices, e_1 fastest
+    lidx = np.indices((ni,) * dim)[::-1]     # local multi-indices, i_1 fastest
+    E = int(np.prod(ns))
+    NP = ni ** dim
+    gi = [(order * eidx[k].reshape(E, 1) + lidx[k].reshape(1, NP)) for k in range(dim)]
+    node = gi[0].astype(np.int64)
+    stride = 1
+    for k in range(1, dim):
+        stride *= M[k - 1]
+        node = node + stride * gi[k]
+    emap = node.astype(np.int32)
+    # boundary nodes fixed in all components
+    on_bnd = np.zeros(Nx, dtype=bool)
+    for k in range(dim):
+        Ik = idx[k].reshape(-1)
+        on_bnd |= (Ik == 0) | (Ik == M[k] - 1)
+    fixed = np.tile(on_bnd.astype(np.uint8), dim)
+    return StructuredMesh(dim, order, ns, x, emap, fixed, M)
+
+
+def perturb_uniform(mesh: StructuredMesh, amp: float = 0.15, seed: int = BASE_SEED) -> StructuredMesh:
+    """Interior nodes displaced by U[-amp h, amp h] per component
+    (the 2D 8x8 Q2 configuration uses amp = 0.15)."""
+    rng = np.random.default_rng(seed)
+    out = mesh.copy()
+    h = mesh.h
+    disp = rng.uniform(-amp * h, amp * h, size=mesh.ndof)
+    out.x = mesh.x + np.where(mesh.fixed != 0, 0.0, disp)
+    return out
+
+
+def perturb_smooth(mesh: StructuredMesh, seed: int = BASE_SEED, amp_smooth: float = 0.1,
+                   amp_noise: float = 0.05) -> StructuredMesh:
+    """Interior nodes displaced by amp_smooth h sin(2 pi k_a . x + phi_a) plus
+    U[-amp_noise h, amp_noise h] per component a, with k_a in {1,2,3}^d and
+    phi_a in [0, 2 pi) drawn per component; x is the unperturbed node."""
+    rng = np.random.default_rng(seed)
+    d, Nx, h = mesh.dim, mesh.num_nodes, mesh.h
+    X = mesh.x.reshape(d, Nx)
+    disp = np.empty((d, Nx))
+    for a in range(d):
+        k = rng.integers(1, 4, size=d)
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        disp[a] = amp_smooth * h * np.sin(2.0 * np.pi * (k @ X) + phi)
+    disp += rng.uniform(-amp_noise * h, amp_noise * h, size=(d, Nx))
+    out = mesh.copy()
+    out.x = mesh.x + np.where(mesh.fixed != 0, 0.0, disp.reshape(-1))
+    return out
+
+
+def rigid_map(mesh: StructuredMesh, R: np.ndarray, scale: float, shift=None) -> np.ndarray:
+    """Positions scale * R x + shift (for invariance tests)."""
+    d, Nx = mesh.dim, mesh.num_nodes
+    X = mesh.x.reshape(d, Nx)
+    Y = scale * (R @ X)
+    if shift is not None:
+        Y = Y + np.asarray(shift).reshape(d, 1)
+    return Y.reshape(-1).copy()
+
+
+def random_rotation(dim: int, seed: int) -> np.ndarray:
+    """A random proper rotation (QR of a Gaussian matrix, det +1)."""
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((dim, dim)))
+    Q = Q @ np.diag(np.sign(np.diag(R)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    return Q
+
+
+# ------------------------------------------------------------------ named configurations
+def config_mesh(cfg: int, seed: int | None = None, n_e: int | None = None, order: int | None = None):
+    """The seeded benchmark meshes.
+
+    1: 2D 8x8 Q2, uniform +-0.15h interior perturbation (metric 2).
+    2: 3D 24^3 Q2, smooth + noise perturbation (metric 302).
+    3: 3D 48^3 Q3, smooth + noise perturbation (metric 303).
+    ``n_e`` / ``order`` override the size for scaled-down cases of the same family.
+    """
+    s = BASE_SEED + cfg if seed is None else seed
+    if cfg == 1:
+        m = structured(2, order or 2, n_e or 8)
+        return perturb_uniform(m, 0.15, s)
+    if cfg == 2:
+        return perturb_smooth(structured(3, order or 2, n_e or 24), s)
+    if cfg == 3:
+        return perturb_smooth(structured(3, order or 3, n_e or 48), s)
+    raise ValueError(cfg)
+
+
+CONFIG_METRIC = {1: 2, 2: 302, 3: 303}
