@@ -1,0 +1,336 @@
+"""Benchmark of the TMOP partially assembled Newton step on B300.
+
+Workload (default): 3D hex mesh 48^3 elements, order p = 3, 4^3 Gauss points
+per element (3,048,625 nodes, 9,145,875 DOFs), seeded smooth + noise
+perturbation, metric mu_303, identity targets, fixed boundary.  One "step"
+is one pass of the whole hot path: energy + min det, gradient, partial
+assembly of d2mu/dT2, Hessian diagonal, exactly 20 Jacobi-MINRES iterations
+(one Hessian action each, the paper's throughput methodology of Sec. 4.1) and
+the backtracking line search, starting every step from the same initial
+positions.
+
+value = DOF x (Hessian actions per step) / step time, in GDOF/s; the
+roofline object reports the Hessian-action kernel alone (CUDA events on the
+library's stream).  Inputs (2.5 GB of stored Hessian data) are larger than
+the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference ...     (the FP64 CPU oracle, bounded sample)
+Under torchrun every rank runs its own replica (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian-apply GDOF/s & %HBM peak (3D hex p=2..4); time-to-converged-mesh, p50/p99"
+UNIT = "GDOF/s"
+FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 rate (profiling recipe table)
+MINRES_ITS = 20
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_apply launch, captured on the
+# 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
+# since the capture.
+TRAFFIC_BYTES = {"fp64": 2.779e9, "fp32": None}
+
+
+def flops_apply_per_elem(d, ni, nq, ns):
+    """Algorithmic flops of one element of the Hessian action: sum-factorised
+    forward and transposed contractions (2 flops per multiply-add) plus the
+    pointwise H:dA with the full d^2 x d^2 matrix."""
+    if d == 3:
+        fwd = 2 * nq * ni ** 3 + 3 * nq ** 2 * ni ** 2 + 3 * nq ** 3 * ni
+        return 2 * (2 * d * fwd) + 2 * (d * d) ** 2 * nq ** 3
+    fwd = 2 * nq * ni ** 2 + 2 * nq ** 2 * ni
+    return 2 * (2 * d * fwd) + 2 * (d * d) ** 2 * nq ** 2
+
+
+def bytes_apply_per_elem(d, ni, nq, ns, rsz):
+    """Algorithmic bytes of one element of the Hessian action: the stored
+    quadrature data (ns values per point), the map, the gathered input and the
+    element-vector output (d (p+1)^d values each)."""
+    np_, nqd = ni ** d, nq ** d
+    return ns * nqd * rsz + np_ * 4 + 2 * d * np_ * rsz
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+        self.f.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.f.name):
+                parts = [s.strip() for s in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def workload(args):
+    from paper_2205_12721_b300 import meshgen
+    m = meshgen.config_mesh(3, n_e=args.n_e, order=args.order)
+    return m
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2205_12721_b300 import capi
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    m = workload(args)
+    d, p, nq = m.dim, m.order, m.order + 1
+    ni = p + 1
+    ns = (d * d) * (d * d + 1) // 2
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        gm = TmopMesh.from_structured(m, capi.METRIC_303, precision=args.precision,
+                                      stream=stream)
+        x0 = torch.from_numpy(m.x).to(dev)
+        x = x0.clone()
+    opts = dict(minres_rtol=0.0, minres_max_it=MINRES_ITS, minres_fixed_its=True)
+
+    def step():
+        x.copy_(x0)
+        r = gm.newton_step(x, **opts)
+        if r["status"] != capi.OK:
+            raise RuntimeError(f"newton step failed: {r}")
+        return r
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    capi.tmop_profile_enable(gm.ctx, True)
+    launches0 = capi.tmop_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            reps = [step() for _ in range(args.steps)]
+            ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = capi.tmop_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    apply_ms, apply_n = capi.tmop_profile_read(gm.ctx, capi.K_APPLY)
+    prof = {name: capi.tmop_profile_read(gm.ctx, k) for name, k in
+            [("energy", capi.K_ENERGY), ("gradient", capi.K_GRADIENT), ("hsetup", capi.K_HSETUP),
+             ("apply", capi.K_APPLY), ("diag", capi.K_DIAG), ("assemble", capi.K_ASSEMBLE)]}
+    capi.tmop_profile_enable(gm.ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = MINRES_ITS
+    value = world * m.ndof * applies / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    xh = torch.from_numpy(m.x).pin_memory()
+    xout = torch.empty_like(xh).pin_memory()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            x.copy_(xh, non_blocking=True)
+            gm.newton_step(x, **opts)
+            xout.copy_(x, non_blocking=True)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            x.copy_(xh, non_blocking=True)
+            r = gm.newton_step(x, **opts)
+            xout.copy_(x, non_blocking=True)
+        stream.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * m.ndof * applies / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(xout.numel() * 8)}
+
+    # roofline of the Hessian-action kernel
+    rsz = 4 if args.precision == "fp32" else 8
+    E = m.num_elems
+    apply_avg_ms = apply_ms / max(apply_n, 1)
+    flops = flops_apply_per_elem(d, ni, nq, ns) * E
+    byts = bytes_apply_per_elem(d, ni, nq, ns, rsz) * E
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    gbs = byts / (apply_avg_ms * 1e-3) / 1e9
+    if args.precision == "fp64":
+        ach = flops / (apply_avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "peak_source": "nominal FP64 rate of the profiling recipe",
+                "kernel": "k_apply<Cfg<3,3,4>,double>", "flops_per_launch": flops,
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm,
+                             "frac": (gbs / hbm) if hbm else None, "bytes_per_launch": byts}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (gbs / hbm) if hbm else None, "traffic": args.traffic,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "kernel": "k_apply<Cfg<3,3,4>,float>", "bytes_per_launch": byts}
+    roof["avg_launch_ms"] = apply_avg_ms
+    roof["launches"] = apply_n
+    roof["apply_gdofs"] = m.ndof / (apply_avg_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 (H, MINRES) / f64",
+        "data": "synthetic seeded perturbed Cartesian mesh (no dataset)",
+        "config": {"workload": f"3D hex {m.n[0]}^3 Q{p}, {nq}^3 Gauss pts, mu_303, identity target, "
+                               f"1 Newton step = energy+grad+PA setup+diag+{MINRES_ITS} MINRES+line search",
+                   "dofs": m.ndof, "elements": E, "precision": args.precision,
+                   "hessian_applies_per_step": applies,
+                   "l2": "inputs larger than L2 (stored d2mu/dT2 "
+                         f"{ns * nq ** d * E * rsz / 1e9:.2f} GB), no flush",
+                   "parallelism": f"replicas x{world} (one mesh per GPU, no collective)"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "kernel_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items()},
+        "newton": {"alpha": reps[-1]["alpha"], "minres_iters": reps[-1]["minres_iters"],
+                   "energy": reps[-1]["energy"], "energy_new": reps[-1]["energy_new"]},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    gm.close()
+    return out
+
+
+def cpu_baseline(args, seconds=None):
+    """The FP64 oracle as it stands (single thread), one Newton step with
+    exactly 20 MINRES iterations on a bounded sample of the workload: the same
+    mesh family at 8^3 elements (1/216 of the 48^3 elements)."""
+    import oracle as O
+    from paper_2205_12721_b300 import meshgen
+    n_s = args.cpu_sample_n
+    m = meshgen.config_mesh(3, n_e=n_s, order=args.order)
+    om = O.Mesh(3, m.order, m.order + 1, m.map, m.num_nodes, 303, m.fixed)
+    x = m.x.copy()
+    t0 = time.perf_counter()
+    r = O.newton_step(om, x, 0.0, MINRES_ITS, True)
+    dt = time.perf_counter() - t0
+    return {"value": m.ndof * MINRES_ITS / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle Newton step (20 MINRES) on the {n_s}^3 Q{m.order} mesh of the "
+                      f"same family ({m.ndof} DOFs), {dt:.2f} s", "status": r["status"]}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args))
+    wall = (time.perf_counter() - t0) / args.steps
+    v = statistics.median(c["value"] for c in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic seeded perturbed Cartesian mesh (no dataset)",
+            "config": {"workload": "3D hex 48^3 Q3, mu_303: each step is the FP64 CPU oracle's "
+                                   f"Newton step on a {args.cpu_sample_n}^3 sample of the same family"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--n-e", dest="n_e", type=int, default=48)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--cpu-sample-n", dest="cpu_sample_n", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="override the ncu dram bytes per launch of the apply kernel")
+    args = ap.parse_args()
+    if args.traffic is None and args.n_e == 48 and args.order == 3:
+        args.traffic = TRAFFIC_BYTES.get(args.precision)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

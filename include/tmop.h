@@ -1,0 +1,214 @@
+/*
+ * tmop.h: C ABI of the B300 (sm_103a) TMOP partial-assembly library.
+ *
+ * The library computes the data-parallel hot path of the target-matrix
+ * optimization paradigm (TMOP) for high-order quadrilateral (2D) and
+ * hexahedral (3D) meshes of order p = 1..4, as described in "Accelerating
+ * High-Order Mesh Optimization Using Finite Element Partial Assembly on
+ * GPUs" (Camier et al.):
+ *   - Jacobians A = sum_i x_{E,i} grad(w_i)^T at the quadrature points by
+ *     sum factorisation, T = A W^-1 (Sec. 2.2 eq. A and eq. T, Sec. 3.2);
+ *   - the energy F = sum_E sum_q w_q det(W) mu(T) (eq. F_full, Sec. 3.3);
+ *   - its nodal gradient dF/dx (eq. vm_pa_grad, Sec. 3.3);
+ *   - partial assembly of d2mu/dT2 at every quadrature point, the Hessian
+ *     action and its diagonal (eq. vm_pa_hess, Sec. 3.4);
+ *   - the Newton step with Jacobi-preconditioned MINRES and the backtracking
+ *     line search that keeps det(A) > 0 (Sec. 2.3, eq. nodal_solve/dx).
+ *
+ * Conventions shared by every call
+ *   - Every array argument is a DEVICE pointer unless marked "host".  The
+ *     caller owns every array it passes; the context owns everything it
+ *     allocates (stored Hessian data, tables, maps, work vectors) and frees it
+ *     in tmop_destroy.
+ *   - Positions and vectors are component-major: x[a * num_nodes + node],
+ *     length dim * num_nodes ("DOF" = dim * num_nodes, the paper's count of
+ *     unique degrees of freedom, Sec. 4.1 table).
+ *   - elem_to_node is num_elems x (order+1)^dim int32 in lexicographic local
+ *     order i = i1 + (p+1) i2 + (p+1)^2 i3 (Sec. 3.1).
+ *   - Reference element [0,1]^dim, Gauss-Legendre quadrature with nq1d points
+ *     per direction, Lagrange basis on Gauss-Lobatto-Legendre nodes.
+ *   - All work is enqueued on the stream given to tmop_setup.  Calls that
+ *     return host scalars synchronise that stream; the others do not.
+ *   - No call aborts or traps: each returns a tmop_status, and
+ *     tmop_last_error() gives a one-line description of the last failure on
+ *     the calling thread.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef TMOP_H
+#define TMOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMOP_OK = 0,
+    TMOP_ERR_ARG = 1,          /* invalid argument or unsupported size */
+    TMOP_ERR_INVERTED = 2,     /* det(A) <= 0 at some quadrature point */
+    TMOP_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    TMOP_ERR_OOM = 4,          /* device allocation failed */
+    TMOP_ERR_MINRES = 5,       /* MINRES breakdown */
+    TMOP_ERR_LINESEARCH = 6,   /* no step length passed the line search */
+    TMOP_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
+    TMOP_ERR_UNSUPPORTED = 8   /* (dim, order, nq1d, metric) not built */
+} tmop_status;
+
+/* Quality metrics (Sec. 2.2; mu_303 in Sec. 4.1).  T = A W^-1, tau = det T.
+ *   TMOP_METRIC_2     (2D) mu = |T|^2 / (2 tau) - 1                 shape
+ *   TMOP_METRIC_302   (3D) mu = |T|^2 |T^-1|^2 / 9 - 1              shape
+ *   TMOP_METRIC_303   (3D) mu = |T|^2 / (3 tau^(2/3)) - 1            shape
+ *   TMOP_METRIC_55    (2D/3D) mu = (tau - 1)^2                       size
+ *   TMOP_METRIC_303_55 (3D) mu_303 + mu_55                          shape+size */
+enum { TMOP_METRIC_2 = 2, TMOP_METRIC_55 = 55, TMOP_METRIC_302 = 302,
+       TMOP_METRIC_303 = 303, TMOP_METRIC_303_55 = 30355 };
+
+/* Targets W (eq. W).  IDENTITY: W = I.  SIZE_FIELD: W = h0 s(x)^(1/dim) I
+ * with s(x) = 1 + 0.5 prod_k sin(2 pi x_k) evaluated at the current physical
+ * quadrature point; W is recomputed whenever positions change and dW/dx is
+ * not differentiated (Sec. 3.6). */
+enum { TMOP_TARGET_IDENTITY = 0, TMOP_TARGET_SIZE_FIELD = 1 };
+
+/* Precision of the stored d2mu/dT2 data, the Hessian action, its diagonal
+ * and the inner MINRES vectors.  Energy, gradient, det(A), the line search
+ * and the outer convergence test are always FP64. */
+enum { TMOP_FP64 = 0, TMOP_FP32 = 1 };
+
+typedef struct {
+    int dim;             /* 2 or 3 */
+    int order;           /* p, 1..4 */
+    int nq1d;            /* quadrature points per direction: p+1 or p+2 */
+    int64_t num_elems;
+    int64_t num_nodes;   /* N_x */
+    int metric;          /* TMOP_METRIC_* valid for dim */
+    int target;          /* TMOP_TARGET_* */
+    double target_h0;    /* h0 of the size target (ignored for IDENTITY) */
+    int hess_precision;  /* TMOP_FP64 or TMOP_FP32 */
+} tmop_desc;
+
+typedef struct {
+    double minres_rtol;     /* stop when ||r||_{M^-1} <= rtol ||b||_{M^-1} */
+    int minres_max_it;      /* iteration cap (the paper uses 50, Sec. 4.1) */
+    int minres_fixed_its;   /* 1: run exactly minres_max_it iterations */
+    double ls_factor;       /* 1.2 in the paper (Sec. 2.3) */
+    int ls_max_halvings;    /* alpha = 1, 1/2, ..., 2^-ls_max_halvings */
+} tmop_solver_opts;
+
+typedef struct {
+    double energy;         /* F(x) before the step */
+    double grad_norm;      /* |dF(x)| before the step (l2, free DOFs) */
+    double energy_new;     /* F(x+) of the accepted step */
+    double grad_norm_new;  /* |dF(x+)| of the accepted step */
+    double alpha;          /* accepted step length (0 if none) */
+    double min_det;        /* min det(A) over quadrature points of x+ */
+    double minres_resid;   /* final ||r||_{M^-1} / ||b||_{M^-1} */
+    int minres_iters;
+    int halvings;
+    int status;            /* tmop_status of the step */
+} tmop_step_report;
+
+typedef struct tmop_ctx tmop_ctx;
+
+/* Build a context for one mesh (Sec. 2.1 mesh, Sec. 3 PA operator
+ * decomposition): 1D tables B1D/G1D (eq. B_G_1D), a device copy of the
+ * element-to-node map, and its transpose (node -> element entries) used for
+ * the deterministic, atomics-free E-vector to L-vector assembly.
+ *   desc          host; sizes and options (see tmop_desc).
+ *   elem_to_node  device int32, num_elems * (order+1)^dim; copied.
+ *   fixed         device uint8, dim * num_nodes (1 = Dirichlet DOF), or NULL
+ *                 for none; copied.  The gradient is zero and the Hessian
+ *                 row/column is the identity on fixed DOFs.
+ *   cuda_stream   a cudaStream_t (NULL = legacy default stream).
+ *   out           host; receives the context.
+ * Errors: TMOP_ERR_ARG (bad sizes, map entry out of range),
+ * TMOP_ERR_UNSUPPORTED, TMOP_ERR_OOM, TMOP_ERR_CUDA. */
+tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const uint8_t *fixed,
+                       void *cuda_stream, tmop_ctx **out);
+
+/* Energy F(x) = 1^T D0(B G x) (Sec. 3.3, eq. D0_expression) and the minimum
+ * of det(A) over all quadrature points.
+ *   x        device FP64, dim * num_nodes.
+ *   F        host; F(x), or +inf when the mesh is inverted.
+ *   min_det  host (may be NULL); min over quadrature points of det(A).
+ * Synchronises the stream.  Returns TMOP_ERR_INVERTED when min det <= 0. */
+tmop_status tmop_energy(tmop_ctx *ctx, const double *x, double *F, double *min_det);
+
+/* Gradient g = dF/dx (Sec. 3.3, eq. vm_pa_grad, general W: the quadrature
+ * data is c_q P(T) W^-T with c_q = w_q det W), assembled to nodes, zero on
+ * fixed DOFs.
+ *   x  device FP64, dim * num_nodes;  g  device FP64, same length (output).
+ * Asynchronous.  An inverted point contributes nothing; call tmop_energy to
+ * detect inversion. */
+tmop_status tmop_gradient(tmop_ctx *ctx, const double *x, double *g);
+
+/* Partial-assembly setup (Sec. 3.4): store, at every quadrature point, the
+ * A-space second derivative H_{ab,ce} = c_q sum_{n,f} d2mu/dT_an dT_cf
+ * W^-1_bn W^-1_ef, d^4 values of which the d^2 (d^2+1)/2 symmetric ones are
+ * kept, in the context's precision.  x: device FP64.  Asynchronous. */
+tmop_status tmop_hessian_setup(tmop_ctx *ctx, const double *x);
+
+/* Hessian action y = d2F v from the stored data (Sec. 3.4, eq. vm_pa_hess):
+ * forward contractions B G v, pointwise H : dA, transposed contractions,
+ * deterministic assembly.  Fixed DOFs: v is treated as zero there on input
+ * and y = v there on output.
+ *   v, y  device, dim * num_nodes, double* for TMOP_FP64 contexts and
+ *         float* for TMOP_FP32 contexts; must not alias.
+ * Requires a previous tmop_hessian_setup.  Asynchronous. */
+tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y);
+
+/* Diagonal of d2F from the stored data by tensor contractions (Sec. 3.4,
+ * Jacobi preconditioning); 1 on fixed DOFs.
+ *   diag  device, dim * num_nodes, double* (FP64 context) or float* (FP32).
+ * Requires a previous tmop_hessian_setup.  Asynchronous. */
+tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag);
+
+/* One Newton step (Sec. 2.3): dx = [d2F]^-1 dF by Jacobi-preconditioned
+ * MINRES (x0 = 0, M^-1 = 1/|diag|), then x+ = x - alpha dx with alpha = 1,
+ * 1/2, ... until det A(x+) > 0 at every point, F(x+) < ls_factor F(x) and
+ * |dF(x+)| < ls_factor |dF(x)|.
+ *   x     device FP64, dim * num_nodes; overwritten only by an accepted step.
+ *   opts  host (NULL = rtol 1e-8, 50 iterations, factor 1.2, 20 halvings).
+ *   rep   host (may be NULL).
+ * Synchronises.  Returns TMOP_ERR_INVERTED if x is inverted,
+ * TMOP_ERR_LINESEARCH if no step length passed (x unchanged),
+ * TMOP_ERR_MINRES on breakdown.  A stationary x (dF = 0) returns TMOP_OK
+ * with alpha = 0. */
+tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *opts,
+                             tmop_step_report *rep);
+
+/* Free the context and everything it owns.  NULL is accepted. */
+void tmop_destroy(tmop_ctx *ctx);
+
+/* Static string for a status code. */
+const char *tmop_status_string(tmop_status st);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *tmop_last_error(void);
+
+/* ---- Instrumentation (not part of the paper's method) ------------------ */
+
+/* Number of kernels this library has launched since load (all contexts). */
+int64_t tmop_launch_count(void);
+
+/* Kernel classes for per-class device timing. */
+enum { TMOP_K_ENERGY = 0, TMOP_K_GRADIENT = 1, TMOP_K_HSETUP = 2, TMOP_K_APPLY = 3,
+       TMOP_K_DIAG = 4, TMOP_K_ASSEMBLE = 5, TMOP_K_VECTOR = 6, TMOP_K_NCLASS = 7 };
+
+/* Enable (1) or disable (0) CUDA-event timing of every element kernel
+ * launch on the context's stream, and reset the accumulated figures. */
+tmop_status tmop_profile_enable(tmop_ctx *ctx, int on);
+
+/* Accumulated device time (ms) and launch count of one kernel class since
+ * profiling was enabled.  Synchronises the stream. */
+tmop_status tmop_profile_read(tmop_ctx *ctx, int kernel_class, double *total_ms,
+                              int64_t *launches);
+
+/* Bytes of device memory the context holds. */
+int64_t tmop_device_bytes(const tmop_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMOP_H */

@@ -1,0 +1,186 @@
+"""Thin ctypes binding of the C ABI in ``include/tmop.h``.
+
+Functions keep the C names (``tmop_setup``, ``tmop_energy``, ...) and only
+marshal arguments: device arrays are ``torch`` CUDA tensors (their
+``data_ptr()`` is passed), host scalars come back as Python floats.  Every
+step of the computation runs in ``libtmop_b300.so``; if the library is missing
+the import fails loudly (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmop_b300.so")
+
+OK, ERR_ARG, ERR_INVERTED, ERR_CUDA, ERR_OOM, ERR_MINRES, ERR_LINESEARCH, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = range(9)
+METRIC_2, METRIC_55, METRIC_302, METRIC_303, METRIC_303_55 = 2, 55, 302, 303, 30355
+TARGET_IDENTITY, TARGET_SIZE_FIELD = 0, 1
+FP64, FP32 = 0, 1
+K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)
+
+# names declared in include/tmop.h (checked by the test-suite)
+EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
+           "tmop_hessian_apply", "tmop_hessian_diag", "tmop_newton_step", "tmop_destroy",
+           "tmop_status_string", "tmop_last_error", "tmop_launch_count", "tmop_profile_enable",
+           "tmop_profile_read", "tmop_device_bytes")
+
+
+class TmopError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({last_error()})")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("nq1d", ctypes.c_int),
+                ("num_elems", ctypes.c_int64), ("num_nodes", ctypes.c_int64),
+                ("metric", ctypes.c_int), ("target", ctypes.c_int),
+                ("target_h0", ctypes.c_double), ("hess_precision", ctypes.c_int)]
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("minres_rtol", ctypes.c_double), ("minres_max_it", ctypes.c_int),
+                ("minres_fixed_its", ctypes.c_int), ("ls_factor", ctypes.c_double),
+                ("ls_max_halvings", ctypes.c_int)]
+
+
+class StepReport(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("grad_norm", ctypes.c_double),
+                ("energy_new", ctypes.c_double), ("grad_norm_new", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("min_det", ctypes.c_double),
+                ("minres_resid", ctypes.c_double), ("minres_iters", ctypes.c_int),
+                ("halvings", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2205_12721_b300/build.py "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "tmop_setup": (I, [ctypes.POINTER(Desc), P, P, P, ctypes.POINTER(P)]),
+            "tmop_energy": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+            "tmop_gradient": (I, [P, P, P]),
+            "tmop_hessian_setup": (I, [P, P]),
+            "tmop_hessian_apply": (I, [P, P, P]),
+            "tmop_hessian_diag": (I, [P, P]),
+            "tmop_newton_step": (I, [P, P, ctypes.POINTER(SolverOpts), ctypes.POINTER(StepReport)]),
+            "tmop_destroy": (None, [P]),
+            "tmop_status_string": (ctypes.c_char_p, [I]),
+            "tmop_last_error": (ctypes.c_char_p, []),
+            "tmop_launch_count": (I64, []),
+            "tmop_profile_enable": (I, [P, I]),
+            "tmop_profile_read": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+            "tmop_device_bytes": (I64, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise TmopError(st, where)
+
+
+def status_string(st: int) -> str:
+    return lib().tmop_status_string(st).decode()
+
+
+def last_error() -> str:
+    return lib().tmop_last_error().decode()
+
+
+def tmop_launch_count() -> int:
+    return lib().tmop_launch_count()
+
+
+def tmop_setup(desc: Desc, elem_to_node, fixed=None, stream=None) -> int:
+    """Returns the context handle (an int).  ``stream``: a torch.cuda.Stream,
+    a raw cudaStream_t int, or None for the current torch stream."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p()
+    _check(lib().tmop_setup(ctypes.byref(desc), _ptr(elem_to_node), _ptr(fixed), stream,
+                            ctypes.byref(out)), "tmop_setup")
+    return out.value
+
+
+def tmop_energy(ctx: int, x, check: bool = True):
+    """(status, F, min det A)."""
+    F = ctypes.c_double(); md = ctypes.c_double()
+    st = lib().tmop_energy(ctx, _ptr(x), ctypes.byref(F), ctypes.byref(md))
+    if check and st not in (OK, ERR_INVERTED):
+        _check(st, "tmop_energy")
+    return st, F.value, md.value
+
+
+def tmop_gradient(ctx: int, x, g):
+    _check(lib().tmop_gradient(ctx, _ptr(x), _ptr(g)), "tmop_gradient")
+
+
+def tmop_hessian_setup(ctx: int, x):
+    _check(lib().tmop_hessian_setup(ctx, _ptr(x)), "tmop_hessian_setup")
+
+
+def tmop_hessian_apply(ctx: int, v, y):
+    _check(lib().tmop_hessian_apply(ctx, _ptr(v), _ptr(y)), "tmop_hessian_apply")
+
+
+def tmop_hessian_diag(ctx: int, diag):
+    _check(lib().tmop_hessian_diag(ctx, _ptr(diag)), "tmop_hessian_diag")
+
+
+def tmop_newton_step(ctx: int, x, opts: SolverOpts | None = None) -> dict:
+    rep = StepReport()
+    st = lib().tmop_newton_step(ctx, _ptr(x), ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(rep))
+    d = rep.as_dict()
+    d["status"] = st
+    return d
+
+
+def tmop_destroy(ctx: int):
+    lib().tmop_destroy(ctx)
+
+
+def tmop_profile_enable(ctx: int, on: bool = True):
+    _check(lib().tmop_profile_enable(ctx, int(on)), "tmop_profile_enable")
+
+
+def tmop_profile_read(ctx: int, kernel_class: int):
+    ms = ctypes.c_double(); n = ctypes.c_int64()
+    _check(lib().tmop_profile_read(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(n)),
+           "tmop_profile_read")
+    return ms.value, n.value
+
+
+def tmop_device_bytes(ctx: int) -> int:
+    return lib().tmop_device_bytes(ctx)

@@ -1,0 +1,635 @@
+// C ABI of the TMOP partial-assembly library: context set-up, the seven
+// entry points of the hot path and the host-driven Newton / MINRES loop.
+// Every arithmetic step runs in the kernels of elem_*.cu and vec_kernels.cu;
+// this file validates arguments, owns device memory and sequences launches.
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tmop_device.cuh"
+#include "tmop_internal.h"
+
+using namespace tmop;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+tmop_status fail(tmop_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+tmop_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TMOP_ERR_OOM : TMOP_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+#define TRY(expr)                                 \
+    do {                                          \
+        tmop_status s_ = (expr);                  \
+        if (s_ != TMOP_OK) return s_;             \
+    } while (0)
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+namespace tmop {
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace tmop
+
+struct tmop_ctx {
+    tmop_desc desc{};
+    int d = 0, p = 0, nq = 0, ni = 0, np = 0, nqd = 0, ns = 0, prec = 0;
+    int64_t E = 0, Nx = 0, ndof = 0, ENP = 0;
+    size_t rsz = 8;
+    cudaStream_t stream = nullptr;
+    // mesh data
+    int32_t *map = nullptr, *csr_ptr = nullptr, *csr_idx = nullptr;
+    uint8_t *fixed = nullptr;
+    double *tab = nullptr;
+    float *tabf = nullptr;
+    // partial assembly data and element vectors
+    void *H = nullptr;
+    bool h_ready = false;
+    double *ev64 = nullptr;
+    void *evR = nullptr;
+    // reductions
+    double *part = nullptr;
+    int64_t part_n = 0;
+    double *scal = nullptr;      // device scalars
+    double *hscal = nullptr;     // pinned host mirror
+    // Newton / MINRES work
+    double *g = nullptr, *dx = nullptr, *xt = nullptr;
+    void *vm = nullptr, *diagR = nullptr, *minv = nullptr;
+    void *kv[8] = {nullptr};     // v, R1, R2, Z, W1, W2, W3, spare
+    MinresState *st = nullptr, *hst = nullptr;
+    int check_every = 4;
+    // instrumentation
+    bool prof = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[TMOP_K_NCLASS] = {0};
+    int64_t prof_n[TMOP_K_NCLASS] = {0};
+    int64_t bytes = 0;
+    std::vector<void *> allocs;
+
+    ElemParams params() const
+    {
+        ElemParams P;
+        P.map = map;
+        P.E = E;
+        P.Nx = Nx;
+        P.tab = tab;
+        P.tabf = tabf;
+        P.metric = desc.metric;
+        P.target = desc.target;
+        P.h0 = desc.target_h0;
+        return P;
+    }
+
+    template <class T>
+    tmop_status alloc(T **ptr, size_t count)
+    {
+        *ptr = nullptr;
+        if (count == 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(TMOP_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+        }
+        allocs.push_back(q);
+        bytes += (int64_t)(count * sizeof(T));
+        *ptr = static_cast<T *>(q);
+        return TMOP_OK;
+    }
+    tmop_status alloc_raw(void **ptr, size_t nbytes)
+    {
+        char *q = nullptr;
+        TRY(alloc(&q, nbytes));
+        *ptr = q;
+        return TMOP_OK;
+    }
+
+    cudaEvent_t event()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+namespace {
+
+// Run one launch, timing it with events on the context stream when enabled.
+template <class F>
+tmop_status timed(tmop_ctx *c, int cls, const char *what, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        a = c->event();
+        b = c->event();
+        cudaEventRecord(a, c->stream);
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (c->prof) {
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({cls, a, b});
+    }
+    return TMOP_OK;
+}
+
+tmop_status prof_resolve(tmop_ctx *c)
+{
+    if (c->pending.empty()) return TMOP_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto &r : c->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_ms[r.cls] += ms;
+        c->prof_n[r.cls] += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+    return TMOP_OK;
+}
+
+bool metric_ok(int m, int d)
+{
+    if (m == TMOP_METRIC_2) return d == 2;
+    if (m == TMOP_METRIC_302 || m == TMOP_METRIC_303 || m == TMOP_METRIC_303_55) return d == 3;
+    return m == TMOP_METRIC_55;
+}
+
+// Energy + min det into ctx->scal[0..1] (device), no sync.
+tmop_status energy_async(tmop_ctx *c, const double *x)
+{
+    const ElemParams P = c->params();
+    const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
+    TRY(timed(c, TMOP_K_ENERGY, "energy kernel",
+              [&] { return launch_energy(c->d, c->p, c->nq, P, x, c->part, c->stream); }));
+    CK(launch_finalize_energy(c->part, nb, c->scal, c->stream));
+    return TMOP_OK;
+}
+
+tmop_status read_scalars(tmop_ctx *c, int n)
+{
+    CK(cudaMemcpyAsync(c->hscal, c->scal, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return TMOP_OK;
+}
+
+tmop_status energy_sync(tmop_ctx *c, const double *x, double *F, double *md)
+{
+    TRY(energy_async(c, x));
+    TRY(read_scalars(c, 2));
+    *md = c->hscal[1];
+    if (!(c->hscal[1] > 0.0) && c->E > 0) {
+        *F = INFINITY;
+        return fail(TMOP_ERR_INVERTED, "det(A) <= 0 at some quadrature point");
+    }
+    *F = c->hscal[0];
+    return TMOP_OK;
+}
+
+tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
+{
+    const ElemParams P = c->params();
+    TRY(timed(c, TMOP_K_GRADIENT, "gradient kernel",
+              [&] { return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->stream); }));
+    TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
+        return launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 0,
+                               c->Nx, c->d, c->ENP, g, TMOP_FP64, nullptr, 0, c->stream);
+    }));
+    return TMOP_OK;
+}
+
+// ||a||_2 for an FP64 vector (synchronises).
+tmop_status norm_sync(tmop_ctx *c, const double *a, double *out)
+{
+    const int nb = reduce_blocks(c->ndof);
+    CK(launch_dot(a, a, TMOP_FP64, c->ndof, c->part, nb, c->stream));
+    CK(launch_finalize_sum(c->part, nb, c->scal + 2, c->stream));
+    CK(cudaMemcpyAsync(c->hscal + 2, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = std::sqrt(std::fmax(c->hscal[2], 0.0));
+    return TMOP_OK;
+}
+
+tmop_status hsetup_async(tmop_ctx *c, const double *x)
+{
+    const ElemParams P = c->params();
+    TRY(timed(c, TMOP_K_HSETUP, "hessian setup kernel",
+              [&] { return launch_hsetup(c->d, c->p, c->nq, P, x, c->H, c->prec, c->stream); }));
+    c->h_ready = true;
+    return TMOP_OK;
+}
+
+// y = H v for a v already zero on fixed DOFs (y = 0 there).
+tmop_status apply_internal(tmop_ctx *c, const void *v, void *y, const int *stop, int k)
+{
+    const ElemParams P = c->params();
+    TRY(timed(c, TMOP_K_APPLY, "apply kernel", [&] {
+        return launch_apply(c->d, c->p, c->nq, P, v, c->H, c->evR, c->prec, stop, k, c->stream);
+    }));
+    TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
+        return launch_assemble(c->evR, c->prec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
+                               c->Nx, c->d, c->ENP, y, c->prec, stop, k, c->stream);
+    }));
+    return TMOP_OK;
+}
+
+tmop_status diag_async(tmop_ctx *c, void *diag)
+{
+    const ElemParams P = c->params();
+    TRY(timed(c, TMOP_K_DIAG, "diag kernel", [&] {
+        return launch_diag(c->d, c->p, c->nq, P, c->H, c->evR, c->prec, c->stream);
+    }));
+    TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
+        return launch_assemble(c->evR, c->prec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 2,
+                               c->Nx, c->d, c->ENP, diag, c->prec, nullptr, 0, c->stream);
+    }));
+    return TMOP_OK;
+}
+
+// Jacobi-preconditioned MINRES for H dx = b (b FP64, zero on fixed DOFs).
+tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int max_it,
+                   int fixed_its, int *iters, double *resid, int *breakdown)
+{
+    const int64_t n = c->ndof;
+    const int pr = c->prec;
+    const size_t vb = c->rsz * (size_t)n;
+    const int nb = reduce_blocks(n);
+    void *v = c->kv[0], *R1 = c->kv[1], *R2 = c->kv[2], *Z = c->kv[3];
+    void *W1 = c->kv[4], *W2 = c->kv[5], *W3 = c->kv[6];
+    CK(cudaMemsetAsync(dx, 0, sizeof(double) * n, c->stream));
+    CK(cudaMemsetAsync(W1, 0, vb, c->stream));
+    CK(cudaMemsetAsync(W2, 0, vb, c->stream));
+    CK(launch_minres_init(b, c->minv, pr, n, R1, R2, Z, c->part, nb, c->stream));
+    CK(launch_minres_start(c->part, nb, c->st, max_it, c->stream));
+    CK(launch_minres_scale(Z, c->st, pr, n, v, c->stream));
+    // (R1, R2, Y) rotate; the first Y is Z
+    void *Y = Z;
+    Z = c->kv[7];
+    int k = 1;
+    for (; k <= max_it; ++k) {
+        TRY(apply_internal(c, v, Z, &c->st->stop_iter, k));
+        CK(launch_lanczos_a(Z, R1, v, c->st, pr, n, k, c->part, nb, c->stream));
+        CK(launch_fin_alpha(c->part, nb, c->st, k, c->stream));
+        // Z holds y; new y = M^-1 y goes to the old R1
+        CK(launch_lanczos_b(Z, R2, c->minv, c->st, pr, n, k, R1, c->part, nb, c->stream));
+        CK(launch_fin_beta(c->part, nb, c->st, k, rtol, fixed_its, c->stream));
+        CK(launch_minres_update(v, W1, W2, W3, dx, R1, c->st, pr, n, k, c->stream));
+        // rotate: r1 <- r2, r2 <- y(Z), ynew lives in old R1 (consumed), freed old Y buffer
+        void *oR1 = R1;
+        R1 = R2;
+        R2 = Z;
+        Z = Y;
+        Y = oR1;
+        void *oW1 = W1;
+        W1 = W2;
+        W2 = W3;
+        W3 = oW1;
+        if (!fixed_its && (k % c->check_every == 0) && k < max_it) {
+            CK(cudaMemcpyAsync(c->hst, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (c->hst->stop_iter <= k) break;
+        }
+    }
+    CK(cudaMemcpyAsync(c->hst, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *iters = c->hst->iters;
+    *resid = (c->hst->beta1 > 0.0) ? c->hst->phibar / c->hst->beta1 : 0.0;
+    *breakdown = c->hst->breakdown;
+    return TMOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tmop_status_string(tmop_status st)
+{
+    switch (st) {
+        case TMOP_OK: return "ok";
+        case TMOP_ERR_ARG: return "invalid argument";
+        case TMOP_ERR_INVERTED: return "inverted element (det(A) <= 0)";
+        case TMOP_ERR_CUDA: return "CUDA error";
+        case TMOP_ERR_OOM: return "out of device memory";
+        case TMOP_ERR_MINRES: return "MINRES breakdown";
+        case TMOP_ERR_LINESEARCH: return "line search failed";
+        case TMOP_ERR_TIMEOUT: return "device wait timed out";
+        case TMOP_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char *tmop_last_error(void) { return g_last_error.c_str(); }
+
+int64_t tmop_launch_count(void) { return g_launches.load(); }
+
+void tmop_destroy(tmop_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    for (void *q : ctx->allocs) cudaFree(q);
+    if (ctx->hscal) cudaFreeHost(ctx->hscal);
+    if (ctx->hst) cudaFreeHost(ctx->hst);
+    delete ctx;
+}
+
+tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const uint8_t *fixed,
+                       void *cuda_stream, tmop_ctx **out)
+{
+    if (!desc || !out) return fail(TMOP_ERR_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    const tmop_desc &D = *desc;
+    if (D.dim != 2 && D.dim != 3) return fail(TMOP_ERR_ARG, "dim must be 2 or 3");
+    if (D.order < 1 || D.order > 4) return fail(TMOP_ERR_UNSUPPORTED, "order must be 1..4");
+    if (!elem_supported(D.dim, D.order, D.nq1d))
+        return fail(TMOP_ERR_UNSUPPORTED, "nq1d must be order+1 or order+2");
+    if (D.num_elems < 0 || D.num_nodes <= 0) return fail(TMOP_ERR_ARG, "bad mesh sizes");
+    if (!metric_ok(D.metric, D.dim)) return fail(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
+    if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
+        return fail(TMOP_ERR_ARG, "unknown target");
+    if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
+        return fail(TMOP_ERR_ARG, "target_h0 must be > 0");
+    if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32)
+        return fail(TMOP_ERR_ARG, "hess_precision must be TMOP_FP64 or TMOP_FP32");
+    if (D.num_elems > 0 && !elem_to_node) return fail(TMOP_ERR_ARG, "elem_to_node is NULL");
+    const int64_t ndof = (int64_t)D.dim * D.num_nodes;
+    int np = 1;
+    for (int k = 0; k < D.dim; ++k) np *= D.order + 1;
+    if (D.num_elems * (int64_t)np >= INT_MAX) return fail(TMOP_ERR_ARG, "mesh too large (E*NP >= 2^31)");
+
+    tmop_ctx *c = new tmop_ctx();
+    c->desc = D;
+    c->d = D.dim;
+    c->p = D.order;
+    c->nq = D.nq1d;
+    c->ni = D.order + 1;
+    c->np = np;
+    c->nqd = 1;
+    for (int k = 0; k < D.dim; ++k) c->nqd *= D.nq1d;
+    c->ns = (c->d * c->d) * (c->d * c->d + 1) / 2;
+    c->prec = D.hess_precision;
+    c->rsz = c->prec == TMOP_FP32 ? 4 : 8;
+    c->E = D.num_elems;
+    c->Nx = D.num_nodes;
+    c->ndof = ndof;
+    c->ENP = D.num_elems * (int64_t)np;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    auto bail = [&](tmop_status st) {
+        std::string m = g_last_error;
+        tmop_destroy(c);
+        g_last_error = m;
+        return st;
+    };
+#define STRY(expr)                                 \
+    do {                                           \
+        tmop_status s_ = (expr);                   \
+        if (s_ != TMOP_OK) return bail(s_);        \
+    } while (0)
+#define SCK(call)                                                  \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call));  \
+    } while (0)
+
+    // element map: validate on the host and build its transpose (CSR)
+    std::vector<int32_t> hmap((size_t)c->ENP);
+    if (c->ENP > 0) {
+        SCK(cudaMemcpyAsync(hmap.data(), elem_to_node, sizeof(int32_t) * c->ENP,
+                            cudaMemcpyDeviceToHost, c->stream));
+        SCK(cudaStreamSynchronize(c->stream));
+    }
+    std::vector<int32_t> ptr((size_t)c->Nx + 1, 0), idx((size_t)c->ENP);
+    for (int64_t j = 0; j < c->ENP; ++j) {
+        const int32_t nd = hmap[j];
+        if (nd < 0 || nd >= c->Nx) {
+            delete c;
+            return fail(TMOP_ERR_ARG, "elem_to_node entry " + std::to_string(j) + " = " +
+                                          std::to_string(nd) + " out of range");
+        }
+        ptr[nd + 1]++;
+    }
+    for (int64_t i = 0; i < c->Nx; ++i) ptr[i + 1] += ptr[i];
+    {
+        std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t j = 0; j < c->ENP; ++j) idx[fill[hmap[j]]++] = (int32_t)j;
+    }
+    STRY(c->alloc(&c->map, c->ENP));
+    STRY(c->alloc(&c->csr_ptr, c->Nx + 1));
+    STRY(c->alloc(&c->csr_idx, c->ENP));
+    if (c->ENP > 0) {
+        SCK(cudaMemcpyAsync(c->map, hmap.data(), sizeof(int32_t) * c->ENP, cudaMemcpyHostToDevice, c->stream));
+        SCK(cudaMemcpyAsync(c->csr_idx, idx.data(), sizeof(int32_t) * c->ENP, cudaMemcpyHostToDevice, c->stream));
+    }
+    SCK(cudaMemcpyAsync(c->csr_ptr, ptr.data(), sizeof(int32_t) * (c->Nx + 1), cudaMemcpyHostToDevice, c->stream));
+    if (fixed) {
+        STRY(c->alloc(&c->fixed, ndof));
+        SCK(cudaMemcpyAsync(c->fixed, fixed, ndof, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // 1D tables: B, G, weights
+    const int tabn = 2 * c->nq * c->ni + c->nq;
+    std::vector<double> tab(tabn);
+    std::vector<float> tabf(tabn);
+    host_basis_tables(c->ni, c->nq, tab.data(), tab.data() + c->nq * c->ni,
+                      tab.data() + 2 * c->nq * c->ni);
+    for (int i = 0; i < tabn; ++i) tabf[i] = (float)tab[i];
+    STRY(c->alloc(&c->tab, tabn));
+    STRY(c->alloc(&c->tabf, tabn));
+    SCK(cudaMemcpyAsync(c->tab, tab.data(), sizeof(double) * tabn, cudaMemcpyHostToDevice, c->stream));
+    SCK(cudaMemcpyAsync(c->tabf, tabf.data(), sizeof(float) * tabn, cudaMemcpyHostToDevice, c->stream));
+    // stored Hessian data, element vectors, reductions, work vectors
+    STRY(c->alloc_raw(&c->H, c->rsz * (size_t)c->E * c->ns * c->nqd));
+    STRY(c->alloc(&c->ev64, (size_t)c->d * c->ENP));
+    if (c->prec == TMOP_FP32) STRY(c->alloc_raw(&c->evR, 4 * (size_t)c->d * c->ENP));
+    else c->evR = c->ev64;
+    const int64_t eb = elem_blocks(c->d, c->p, c->nq, c->E);
+    c->part_n = std::max<int64_t>(2 * eb, 2 * 1184);
+    STRY(c->alloc(&c->part, c->part_n));
+    STRY(c->alloc(&c->scal, 8));
+    STRY(c->alloc((double **)&c->st, sizeof(MinresState) / sizeof(double) + 1));
+    STRY(c->alloc(&c->g, ndof));
+    STRY(c->alloc(&c->dx, ndof));
+    STRY(c->alloc(&c->xt, ndof));
+    STRY(c->alloc_raw(&c->vm, c->rsz * ndof));
+    STRY(c->alloc_raw(&c->diagR, c->rsz * ndof));
+    STRY(c->alloc_raw(&c->minv, c->rsz * ndof));
+    for (int i = 0; i < 8; ++i) STRY(c->alloc_raw(&c->kv[i], c->rsz * ndof));
+    SCK(cudaMallocHost((void **)&c->hscal, 8 * sizeof(double)));
+    SCK(cudaMallocHost((void **)&c->hst, sizeof(MinresState)));
+    SCK(cudaStreamSynchronize(c->stream));
+#undef STRY
+#undef SCK
+    *out = c;
+    return TMOP_OK;
+}
+
+tmop_status tmop_energy(tmop_ctx *ctx, const double *x, double *F, double *min_det)
+{
+    if (!ctx || !x || !F) return fail(TMOP_ERR_ARG, "NULL argument");
+    double md = INFINITY;
+    tmop_status st = energy_sync(ctx, x, F, &md);
+    if (min_det) *min_det = md;
+    return st;
+}
+
+tmop_status tmop_gradient(tmop_ctx *ctx, const double *x, double *g)
+{
+    if (!ctx || !x || !g) return fail(TMOP_ERR_ARG, "NULL argument");
+    return gradient_async(ctx, x, g);
+}
+
+tmop_status tmop_hessian_setup(tmop_ctx *ctx, const double *x)
+{
+    if (!ctx || !x) return fail(TMOP_ERR_ARG, "NULL argument");
+    return hsetup_async(ctx, x);
+}
+
+tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y)
+{
+    if (!ctx || !v || !y) return fail(TMOP_ERR_ARG, "NULL argument");
+    if (v == y) return fail(TMOP_ERR_ARG, "v and y must not alias");
+    if (!ctx->h_ready) return fail(TMOP_ERR_ARG, "tmop_hessian_setup has not been called");
+    CK(launch_mask(v, ctx->fixed, ctx->ndof, ctx->vm, ctx->prec, ctx->stream));
+    const ElemParams P = ctx->params();
+    TRY(timed(ctx, TMOP_K_APPLY, "apply kernel", [&] {
+        return launch_apply(ctx->d, ctx->p, ctx->nq, P, ctx->vm, ctx->H, ctx->evR, ctx->prec,
+                            nullptr, 0, ctx->stream);
+    }));
+    TRY(timed(ctx, TMOP_K_ASSEMBLE, "assemble", [&] {
+        return launch_assemble(ctx->evR, ctx->prec, ctx->csr_ptr, ctx->csr_idx, ctx->fixed, v, 1,
+                               ctx->Nx, ctx->d, ctx->ENP, y, ctx->prec, nullptr, 0, ctx->stream);
+    }));
+    return TMOP_OK;
+}
+
+tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag)
+{
+    if (!ctx || !diag) return fail(TMOP_ERR_ARG, "NULL argument");
+    if (!ctx->h_ready) return fail(TMOP_ERR_ARG, "tmop_hessian_setup has not been called");
+    return diag_async(ctx, diag);
+}
+
+tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opts,
+                             tmop_step_report *rep)
+{
+    if (!c || !x) return fail(TMOP_ERR_ARG, "NULL argument");
+    tmop_solver_opts o = {1e-8, 50, 0, 1.2, 20};
+    if (opts) o = *opts;
+    if (o.minres_max_it < 0 || o.ls_max_halvings < 0) return fail(TMOP_ERR_ARG, "negative iteration limit");
+    tmop_step_report r;
+    std::memset(&r, 0, sizeof(r));
+    auto finish = [&](tmop_status st) {
+        r.status = st;
+        if (rep) *rep = r;
+        return st;
+    };
+    double F0 = 0, md0 = 0;
+    tmop_status st = energy_sync(c, x, &F0, &md0);
+    r.energy = F0;
+    r.min_det = md0;
+    if (st != TMOP_OK) return finish(st);
+    st = gradient_async(c, x, c->g);
+    if (st != TMOP_OK) return finish(st);
+    double g0 = 0;
+    st = norm_sync(c, c->g, &g0);
+    if (st != TMOP_OK) return finish(st);
+    r.grad_norm = g0;
+    if (g0 == 0.0) {
+        r.energy_new = F0;
+        r.grad_norm_new = 0.0;
+        return finish(TMOP_OK);
+    }
+    if ((st = hsetup_async(c, x)) != TMOP_OK) return finish(st);
+    if ((st = diag_async(c, c->diagR)) != TMOP_OK) return finish(st);
+    {
+        cudaError_t e = launch_jacobi(c->diagR, c->prec, c->ndof, c->minv, c->stream);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "jacobi"));
+    }
+    int its = 0, brk = 0;
+    double res = 0;
+    st = minres(c, c->g, c->dx, o.minres_rtol, o.minres_max_it, o.minres_fixed_its, &its, &res, &brk);
+    if (st != TMOP_OK) return finish(st);
+    r.minres_iters = its;
+    r.minres_resid = res;
+    if (brk) return finish(fail(TMOP_ERR_MINRES, "MINRES breakdown (preconditioner not positive)"));
+    double alpha = 1.0;
+    for (int h = 0; h <= o.ls_max_halvings; ++h, alpha *= 0.5) {
+        cudaError_t e = launch_trial(x, c->dx, alpha, c->ndof, c->xt, c->stream);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "trial"));
+        double F1 = 0, md1 = 0;
+        st = energy_sync(c, c->xt, &F1, &md1);
+        if (st == TMOP_ERR_INVERTED) continue;            // det A(x+) > 0 required
+        if (st != TMOP_OK) return finish(st);
+        if (!(F1 < o.ls_factor * F0)) continue;           // energy test
+        if ((st = gradient_async(c, c->xt, c->g)) != TMOP_OK) return finish(st);
+        double g1 = 0;
+        if ((st = norm_sync(c, c->g, &g1)) != TMOP_OK) return finish(st);
+        if (!(g1 < o.ls_factor * g0)) continue;           // gradient test
+        e = cudaMemcpyAsync(x, c->xt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "accept"));
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return finish(cuda_fail(e, "accept"));
+        r.alpha = alpha;
+        r.halvings = h;
+        r.energy_new = F1;
+        r.grad_norm_new = g1;
+        r.min_det = md1;
+        g_last_error.clear();
+        return finish(TMOP_OK);
+    }
+    return finish(fail(TMOP_ERR_LINESEARCH, "no step length passed the line search"));
+}
+
+tmop_status tmop_profile_enable(tmop_ctx *ctx, int on)
+{
+    if (!ctx) return fail(TMOP_ERR_ARG, "NULL context");
+    TRY(prof_resolve(ctx));
+    for (int i = 0; i < TMOP_K_NCLASS; ++i) { ctx->prof_ms[i] = 0; ctx->prof_n[i] = 0; }
+    ctx->prof = on != 0;
+    return TMOP_OK;
+}
+
+tmop_status tmop_profile_read(tmop_ctx *ctx, int cls, double *total_ms, int64_t *launches)
+{
+    if (!ctx || cls < 0 || cls >= TMOP_K_NCLASS) return fail(TMOP_ERR_ARG, "bad argument");
+    TRY(prof_resolve(ctx));
+    if (total_ms) *total_ms = ctx->prof_ms[cls];
+    if (launches) *launches = ctx->prof_n[cls];
+    return TMOP_OK;
+}
+
+int64_t tmop_device_bytes(const tmop_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// Hessian-action kernels (the dominant kernel of the Newton step).
+#include "elem_launch.cuh"
+
+namespace tmop {
+
+template <class C, class R>
+static cudaError_t run_apply(const ElemParams &P, const R *v, const R *H, R *ev, const int *stop,
+                             int k, cudaStream_t s)
+{
+    using L = Layout<C, R>;
+    const int64_t nb = grid_of<C>(P.E);
+    if (nb == 0) return cudaSuccess;
+    cudaError_t e = prepare(k_apply<C, R>, L::bytes);
+    if (e != cudaSuccess) return e;
+    k_apply<C, R><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class C>
+static cudaError_t run_apply_any(const ElemParams &P, const void *v, const void *H, void *ev,
+                                 int prec, const int *stop, int k, cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        return run_apply<C, float>(P, static_cast<const float *>(v), static_cast<const float *>(H),
+                                   static_cast<float *>(ev), stop, k, s);
+    return run_apply<C, double>(P, static_cast<const double *>(v), static_cast<const double *>(H),
+                                static_cast<double *>(ev), stop, k, s);
+}
+
+cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
+                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s)
+{
+#define CASE(D_, P_, Q_) \
+    case TMOP_KEY(D_, P_, Q_): return run_apply_any<Cfg<D_, P_, Q_>>(P, v, H, ev, prec, stop_iter, k, s);
+    TMOP_SWITCH(d, p, q, CASE)
+#undef CASE
+}
+
+}  // namespace tmop

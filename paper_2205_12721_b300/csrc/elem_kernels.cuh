@@ -1,0 +1,345 @@
+// Element kernels of the TMOP partial-assembly path (sm_103a).
+//
+//   k_energy    Jacobians + energy sum_q c_q mu(T) + min det A per CTA
+//               (paper Sec. 3.3, eq. D0_expression; line-search check Sec. 2.3)
+//   k_gradient  Jacobians + c_q dmu/dT W^-T + transposed contractions to an
+//               element vector (Sec. 3.3, eq. vm_pa_grad)
+//   k_hsetup    Jacobians + c_q d2mu/dT2 contracted with W^-1 (packed
+//               symmetric d^2(d^2+1)/2 values per point) (Sec. 3.4)
+//   k_apply     forward contractions of v, pointwise H : dA with the stored
+//               data, transposed contractions (Sec. 3.4, eq. vm_pa_hess)
+//   k_diag      diagonal of the Hessian from the stored data through
+//               products of 1D tables (Sec. 3.4)
+// Element vectors (E-vectors) are written as ev[a * E * NP + e * NP + i] and
+// assembled to nodes by the transposed-map kernel in vec_kernels.cu.
+#pragma once
+
+#include "tmop_device.cuh"
+
+namespace tmop {
+
+template <class C, class R>
+struct ElemCtx {
+    R *B, *G, *w;
+    R *su, *s1, *s2, *sA, *sX;
+    int *smap;
+    int t, tx, ty;
+    int64_t e;
+    bool valid;
+};
+
+// Stage the tables and the element map; set up the thread's element slot.
+template <class C, class R>
+__device__ __forceinline__ void prologue(const ElemParams &P, const R *__restrict__ tab,
+                                         unsigned char *smem, ElemCtx<C, R> &c)
+{
+    using L = Layout<C, R>;
+    R *base = reinterpret_cast<R *>(smem);
+    for (int i = threadIdx.x; i < L::TAB; i += C::NT) base[i] = tab[i];
+    c.B = base;
+    c.G = base + C::NQ * C::NI;
+    c.w = base + 2 * C::NQ * C::NI;
+    const int slot = threadIdx.x / C::TPE;
+    const bool act = slot < C::EPB;
+    const int sl = act ? slot : 0;
+    c.t = threadIdx.x - slot * C::TPE;
+    c.tx = c.t % C::MX;
+    c.ty = c.t / C::MX;
+    R *s = base + L::TAB_PAD + sl * L::SLOT;
+    c.su = s;
+    c.s1 = s + C::SU;
+    c.s2 = c.s1 + C::S1;
+    c.sA = c.s2 + C::S2;
+    c.sX = c.sA + C::DD * C::NQD;
+    c.smap = reinterpret_cast<int *>(base + L::TAB_PAD + C::EPB * L::SLOT) + sl * C::NP;
+    c.e = (int64_t)blockIdx.x * C::EPB + sl;
+    c.valid = act && c.e < P.E;
+    if (c.valid)
+        for (int i = c.t; i < C::NP; i += C::TPE) c.smap[i] = P.map[c.e * C::NP + i];
+    __syncthreads();
+}
+
+// Gather one component of an L-vector into the slot and run the forward
+// contractions: sA[(a*D + b)*NQD + q] = d u_a / d xbar_b at q; sX holds the
+// interpolated values when xv is requested.
+template <class C, class R, class RIN>
+__device__ __forceinline__ void forward_component(const ElemParams &P, ElemCtx<C, R> &c,
+                                                  const RIN *__restrict__ u, int a, bool want_x)
+{
+    if (c.valid)
+        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = (R)u[a * P.Nx + c.smap[i]];
+    __syncthreads();
+    R *A0 = c.sA + (a * C::D) * C::NQD;
+    R *xv = want_x ? c.sX + a * C::NQD : nullptr;
+    if (C::D == 3)
+        fwd3<C, R>(c.B, c.G, c.su, c.s1, c.s2, A0, A0 + C::NQD, A0 + 2 * C::NQD, xv, c.tx, c.ty,
+                   c.valid);
+    else
+        fwd2<C, R>(c.B, c.G, c.su, c.s1, A0, A0 + C::NQD, xv, c.tx, c.ty, c.valid);
+}
+
+// Transposed contractions of sA[(a*D + b)*NQD + q] (b = derivative
+// direction) and store of the element vector component a.
+template <class C, class R, class ROUT>
+__device__ __forceinline__ void backward_component(const ElemParams &P, ElemCtx<C, R> &c,
+                                                   ROUT *__restrict__ ev, int a)
+{
+    const R *Y0 = c.sA + (a * C::D) * C::NQD;
+    if (C::D == 3)
+        bwd3<C, R>(c.B, c.G, Y0, Y0 + C::NQD, Y0 + 2 * C::NQD, c.s1, c.s2, c.su, c.tx, c.ty,
+                   c.valid);
+    else
+        bwd2<C, R>(c.B, c.G, Y0, Y0 + C::NQD, c.s1, c.su, c.tx, c.ty, c.valid);
+    if (c.valid)
+        for (int i = c.t; i < C::NP; i += C::TPE)
+            ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = (ROUT)c.su[i];
+}
+
+// Iterate over this thread's quadrature points: (q1, q2) = (tx, ty), all q3.
+template <class C, class F>
+__device__ __forceinline__ void for_my_points(int tx, int ty, bool valid, F &&f)
+{
+    if (!valid || tx >= C::NQ || ty >= C::NQ) return;
+    if (C::D == 3) {
+#pragma unroll 1
+        for (int q3 = 0; q3 < C::NQ; ++q3) f((q3 * C::NQ + ty) * C::NQ + tx, q3);
+    } else {
+        f(ty * C::NQ + tx, 0);
+    }
+}
+
+template <class C>
+__device__ __forceinline__ double point_weight(const double *w, int tx, int ty, int q3)
+{
+    return C::D == 3 ? w[tx] * w[ty] * w[q3] : w[tx] * w[ty];
+}
+
+template <class C>
+__device__ __forceinline__ double point_target(const ElemParams &P, const double *sX, int q)
+{
+    double xq[3] = {0, 0, 0};
+    if (P.target == TGT_SIZE)
+#pragma unroll
+        for (int k = 0; k < C::D; ++k) xq[k] = sX[k * C::NQD + q];
+    return target_scale<C::D>(P.target, P.h0, xq);
+}
+
+// ---------------------------------------------------------------- energy
+template <class C>
+__global__ void __launch_bounds__(C::NT)
+k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ElemCtx<C, double> c;
+    prologue<C, double>(P, P.tab, smem, c);
+    const bool want_x = P.target == TGT_SIZE;
+    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+
+    double esum = 0.0, emin = INFINITY;
+    for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
+        double A[C::DD], T[C::DD], Cf[C::DD];
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) A[r] = c.sA[r * C::NQD + q];
+        const double ws = point_target<C>(P, c.sX, q);
+        double wd = ws;
+#pragma unroll
+        for (int k = 1; k < C::D; ++k) wd *= ws;
+        const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) T[r] = A[r] / ws;
+        double I1, tau, I2;
+        invariants<C::D>(T, I1, tau, I2, Cf);
+        const double detA = tau * wd;
+        emin = fmin(emin, detA);
+        if (detA > 0.0) {
+            Inv v;
+            esum += cq * metric_scalars(P.metric, I1, tau, I2, v);
+        }
+    });
+
+    // deterministic CTA reduction: warps, then warp 0
+    __shared__ double red_s[C::NT / 32], red_m[C::NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        esum += __shfl_down_sync(0xffffffffu, esum, o);
+        emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red_s[wid] = esum; red_m[wid] = emin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, m = INFINITY;
+        for (int i = 0; i < C::NT / 32; ++i) { s += red_s[i]; m = fmin(m, red_m[i]); }
+        part[2 * blockIdx.x] = s;
+        part[2 * blockIdx.x + 1] = m;
+    }
+}
+
+// ---------------------------------------------------------------- gradient
+template <class C>
+__global__ void __launch_bounds__(C::NT)
+k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ElemCtx<C, double> c;
+    prologue<C, double>(P, P.tab, smem, c);
+    const bool want_x = P.target == TGT_SIZE;
+    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+
+    for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
+        double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
+        const double ws = point_target<C>(P, c.sX, q);
+        double wd = ws;
+#pragma unroll
+        for (int k = 1; k < C::D; ++k) wd *= ws;
+        const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) T[r] = c.sA[r * C::NQD + q] / ws;
+        double I1, tau, I2;
+        invariants<C::D>(T, I1, tau, I2, Cf);
+        if (!(tau > 0.0)) {                               // inverted points contribute 0
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = 0.0;
+            return;
+        }
+        Inv v;
+        metric_scalars(P.metric, I1, tau, I2, v);
+        if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
+        const double sc = cq / ws;
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) {
+            double pr = v.f1 * 2.0 * T[r] + v.ft * Cf[r];
+            if (C::D == 3 && v.f2 != 0.0) pr += v.f2 * g2[r];
+            c.sA[r * C::NQD + q] = sc * pr;
+        }
+    });
+    __syncthreads();
+    for (int a = 0; a < C::D; ++a) backward_component<C, double, double>(P, c, ev, a);
+}
+
+// ---------------------------------------------------------------- Hessian setup
+template <class C, class RH>
+__global__ void __launch_bounds__(C::NT)
+k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ElemCtx<C, double> c;
+    prologue<C, double>(P, P.tab, smem, c);
+    const bool want_x = P.target == TGT_SIZE;
+    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+
+    RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
+        double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
+        const double ws = point_target<C>(P, c.sX, q);
+        double wd = ws;
+#pragma unroll
+        for (int k = 1; k < C::D; ++k) wd *= ws;
+        const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) T[r] = c.sA[r * C::NQD + q] / ws;
+        double I1, tau, I2;
+        invariants<C::D>(T, I1, tau, I2, Cf);
+        if (!(tau > 0.0)) {                               // inverted points store 0
+#pragma unroll
+            for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = (RH)0;
+            return;
+        }
+        Inv v;
+        metric_scalars(P.metric, I1, tau, I2, v);
+        if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
+        const double sc = cq / (ws * ws);
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+            for (int s = r; s < C::DD; ++s)
+                He[pidx<C::DD>(r, s) * C::NQD + q] =
+                    (RH)(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+    });
+}
+
+// ---------------------------------------------------------------- Hessian action
+// v is expected to be zero on fixed DOFs (callers mask it first).
+// If stop_iter != nullptr and *stop_iter < k the launch does nothing (MINRES
+// iterations after convergence).
+template <class C, class R>
+__global__ void __launch_bounds__(C::NT)
+k_apply(ElemParams P, const R *__restrict__ v, const R *__restrict__ H, R *__restrict__ ev,
+        const int *__restrict__ stop_iter, int k)
+{
+    if (stop_iter && *stop_iter < k) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    ElemCtx<C, R> c;
+    const R *tab = sizeof(R) == 8 ? reinterpret_cast<const R *>(P.tab)
+                                  : reinterpret_cast<const R *>(P.tabf);
+    prologue<C, R>(P, tab, smem, c);
+    for (int a = 0; a < C::D; ++a) forward_component<C, R, R>(P, c, v, a, false);
+
+    const R *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
+        R dA[C::DD], h[C::NS];
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) dA[r] = c.sA[r * C::NQD + q];
+#pragma unroll
+        for (int s = 0; s < C::NS; ++s) h[s] = He[s * C::NQD + q];
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) {
+            R y = 0;
+#pragma unroll
+            for (int s = 0; s < C::DD; ++s) y += h[r <= s ? pidx<C::DD>(r, s) : pidx<C::DD>(s, r)] * dA[s];
+            c.sA[r * C::NQD + q] = y;
+        }
+    });
+    __syncthreads();
+    for (int a = 0; a < C::D; ++a) backward_component<C, R, R>(P, c, ev, a);
+}
+
+// ---------------------------------------------------------------- diagonal
+// diag_{a,i} = sum_q sum_{b,e} H_{ab,ae}(q) d_b w_i(q) d_e w_i(q); the
+// product d_b w_i d_e w_i factors per direction k into (B or G)(B or G).
+template <class C, class R>
+__global__ void __launch_bounds__(C::NT)
+k_diag(ElemParams P, const R *__restrict__ H, R *__restrict__ ev)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    ElemCtx<C, R> c;
+    const R *tab = sizeof(R) == 8 ? reinterpret_cast<const R *>(P.tab)
+                                  : reinterpret_cast<const R *>(P.tabf);
+    prologue<C, R>(P, tab, smem, c);
+    __shared__ R tbl[3][C::NQ * C::NI];          // B*B, B*G, G*G (elementwise)
+    for (int i = threadIdx.x; i < C::NQ * C::NI; i += C::NT) {
+        tbl[0][i] = c.B[i] * c.B[i];
+        tbl[1][i] = c.B[i] * c.G[i];
+        tbl[2][i] = c.G[i] * c.G[i];
+    }
+    __syncthreads();
+    const R *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    R *f = c.sA;
+    for (int a = 0; a < C::D; ++a) {
+        if (c.valid)
+            for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = 0;
+        for (int b = 0; b < C::D; ++b)
+            for (int e2 = b; e2 < C::D; ++e2) {
+                const int r = a * C::D + b, s = a * C::D + e2;
+                const R scale = (b == e2) ? R(1) : R(2);
+                for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
+                    f[q] = scale * He[pidx<C::DD>(r, s) * C::NQD + q];
+                });
+                __syncthreads();
+                const R *T1 = tbl[(b == 0) + (e2 == 0)];
+                const R *T2 = tbl[(b == 1) + (e2 == 1)];
+                if (C::D == 3) {
+                    const R *T3 = tbl[(b == 2) + (e2 == 2)];
+                    bwd3_tab<C, R>(T1, T2, T3, f, c.s1, c.s2, c.su, c.tx, c.ty, c.valid);
+                } else {
+                    bwd2_tab<C, R>(T1, T2, f, c.s1, c.su, c.tx, c.ty, c.valid);
+                }
+            }
+        if (c.valid)
+            for (int i = c.t; i < C::NP; i += C::TPE)
+                ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = c.su[i];
+        __syncthreads();
+    }
+}
+
+}  // namespace tmop

@@ -1,0 +1,508 @@
+// Device building blocks of the TMOP partial-assembly kernels (sm_103a).
+//
+// One CTA processes EPB elements; each element is owned by TPE = MX*MX
+// threads (MX = max(p+1, nq1d)) laid out as a (tx, ty) square.  The 1D
+// tables B1D/G1D (paper Sec. 3.1, eq. B_G_1D) and the element's nodal block
+// live in shared memory.  Jacobians at the quadrature points are obtained by
+// sum factorisation (Sec. 3.2): one 1D contraction per direction, each
+// O(p^{d+1}); the transposed contractions return quadrature data to the
+// nodes (Sec. 3.3 and 3.4).  In 3D a thread owning (q1, q2) walks the q3
+// column, so the last contraction of each direction stays in registers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tmop {
+
+enum { MET_2 = 2, MET_55 = 55, MET_302 = 302, MET_303 = 303, MET_303_55 = 30355 };
+enum { TGT_IDENTITY = 0, TGT_SIZE = 1 };
+
+template <int D_, int P_, int Q_>
+struct Cfg {
+    static constexpr int D = D_, P = P_, NI = P_ + 1, NQ = Q_;
+    static constexpr int MX = NI > NQ ? NI : NQ;
+    static constexpr int NP = D == 3 ? NI * NI * NI : NI * NI;
+    static constexpr int NQD = D == 3 ? NQ * NQ * NQ : NQ * NQ;
+    static constexpr int DD = D * D;
+    static constexpr int NS = DD * (DD + 1) / 2;            // packed symmetric H
+    static constexpr int TPE = MX * MX;                      // threads per element
+    // elements per CTA: ~128 threads in 3D, ~256 in 2D
+    static constexpr int EPB_ = (D == 3 ? 128 : 256) / TPE;
+    static constexpr int EPB = EPB_ < 1 ? 1 : EPB_;
+    static constexpr int NT = ((EPB * TPE + 31) / 32) * 32;  // CTA size, whole warps
+    // per-element shared scratch (in elements of the compute type)
+    static constexpr int SU = NP > NQD ? NP : NQD;
+    static constexpr int S1 = D == 3 ? 2 * NI * NI * NQ : 2 * NI * NQ;
+    static constexpr int S2 = D == 3 ? 3 * NI * NQ * NQ : 0;
+};
+
+// Kernel parameters shared by every element kernel.
+struct ElemParams {
+    const int32_t *__restrict__ map;   // E x NP
+    int64_t E, Nx;
+    const double *__restrict__ tab;    // B[NQ*NI], G[NQ*NI], w1d[NQ]
+    const float *__restrict__ tabf;    // same, FP32
+    int metric, target;
+    double h0;
+};
+
+// Shared-memory layout of one CTA: tables, then EPB element slots, then maps.
+template <class C, class R>
+struct Layout {
+    static constexpr int TAB = 2 * C::NQ * C::NI + C::NQ;                  // B, G, w
+    static constexpr int TAB_PAD = (TAB + 1) & ~1;
+    static constexpr int SLOT_BASE = C::SU + C::S1 + C::S2 + C::DD * C::NQD;
+    static constexpr int SLOT = (SLOT_BASE + C::D * C::NQD + 1) & ~1;      // + physical coords
+    static constexpr size_t bytes = sizeof(R) * (size_t)(TAB_PAD + C::EPB * SLOT) +
+                                    sizeof(int) * (size_t)(C::EPB * C::NP);
+};
+
+// -------------------------------------------------------------------------
+// Sum-factorised contractions.  All threads of the CTA call these (they
+// contain __syncthreads); threads outside an element's active square idle.
+// Index conventions: nodes u[(i3*NI + i2)*NI + i1], quadrature points
+// f[(q3*NQ + q2)*NQ + q1]; B[q*NI + i].
+// -------------------------------------------------------------------------
+
+// 3D: node values u -> reference gradient components a0 = d/dxbar1,
+// a1 = d/dxbar2, a2 = d/dxbar3 and (optionally) values xv at the points.
+template <class C, class R>
+__device__ __forceinline__ void fwd3(const R *__restrict__ B, const R *__restrict__ G,
+                                     const R *u, R *s1, R *s2, R *a0, R *a1, R *a2, R *xv,
+                                     int tx, int ty, bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ;
+    constexpr int O1 = NI * NI * NQ, O2 = NI * NQ * NQ;
+    if (act && tx < NQ && ty < NI) {          // contract i1 -> q1
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R b = 0, g = 0;
+#pragma unroll
+            for (int i1 = 0; i1 < NI; ++i1) {
+                const R v = u[(i3 * NI + ty) * NI + i1];
+                b += B[tx * NI + i1] * v;
+                g += G[tx * NI + i1] * v;
+            }
+            s1[(i3 * NI + ty) * NQ + tx] = b;
+            s1[O1 + (i3 * NI + ty) * NQ + tx] = g;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NQ && ty < NQ) {          // contract i2 -> q2
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R bb = 0, bg = 0, gb = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < NI; ++i2) {
+                const R sb = s1[(i3 * NI + i2) * NQ + tx];
+                const R sg = s1[O1 + (i3 * NI + i2) * NQ + tx];
+                const R Bq = B[ty * NI + i2], Gq = G[ty * NI + i2];
+                bb += Bq * sb;
+                bg += Gq * sb;
+                gb += Bq * sg;
+            }
+            s2[(i3 * NQ + ty) * NQ + tx] = gb;
+            s2[O2 + (i3 * NQ + ty) * NQ + tx] = bg;
+            s2[2 * O2 + (i3 * NQ + ty) * NQ + tx] = bb;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NQ && ty < NQ) {          // contract i3 -> q3 (column in registers)
+        R c0[NI], c1[NI], c2[NI];
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            c0[i3] = s2[(i3 * NQ + ty) * NQ + tx];
+            c1[i3] = s2[O2 + (i3 * NQ + ty) * NQ + tx];
+            c2[i3] = s2[2 * O2 + (i3 * NQ + ty) * NQ + tx];
+        }
+#pragma unroll
+        for (int q3 = 0; q3 < NQ; ++q3) {
+            R r0 = 0, r1 = 0, r2 = 0, rx = 0;
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                const R Bq = B[q3 * NI + i3], Gq = G[q3 * NI + i3];
+                r0 += Bq * c0[i3];
+                r1 += Bq * c1[i3];
+                r2 += Gq * c2[i3];
+                rx += Bq * c2[i3];
+            }
+            const int q = (q3 * NQ + ty) * NQ + tx;
+            a0[q] = r0;
+            a1[q] = r1;
+            a2[q] = r2;
+            if (xv) xv[q] = rx;
+        }
+    }
+    __syncthreads();
+}
+
+// 3D transpose: out_i = sum_q [y0 d1w_i + y1 d2w_i + y2 d3w_i](q).
+template <class C, class R>
+__device__ __forceinline__ void bwd3(const R *__restrict__ B, const R *__restrict__ G,
+                                     const R *y0, const R *y1, const R *y2, R *s1, R *s2,
+                                     R *out, int tx, int ty, bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ;
+    constexpr int O1 = NI * NI * NQ, O2 = NI * NQ * NQ;
+    if (act && tx < NQ && ty < NQ) {          // q3 -> i3
+        R c0[NQ], c1[NQ], c2[NQ];
+#pragma unroll
+        for (int q3 = 0; q3 < NQ; ++q3) {
+            const int q = (q3 * NQ + ty) * NQ + tx;
+            c0[q3] = y0[q];
+            c1[q3] = y1[q];
+            c2[q3] = y2[q];
+        }
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R z0 = 0, z1 = 0, z2 = 0;
+#pragma unroll
+            for (int q3 = 0; q3 < NQ; ++q3) {
+                const R Bq = B[q3 * NI + i3], Gq = G[q3 * NI + i3];
+                z0 += Bq * c0[q3];
+                z1 += Bq * c1[q3];
+                z2 += Gq * c2[q3];
+            }
+            s2[(i3 * NQ + ty) * NQ + tx] = z0;
+            s2[O2 + (i3 * NQ + ty) * NQ + tx] = z1;
+            s2[2 * O2 + (i3 * NQ + ty) * NQ + tx] = z2;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NQ && ty < NI) {          // q2 -> i2
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R a = 0, b = 0;
+#pragma unroll
+            for (int q2 = 0; q2 < NQ; ++q2) {
+                const R Bq = B[q2 * NI + ty], Gq = G[q2 * NI + ty];
+                a += Bq * s2[(i3 * NQ + q2) * NQ + tx];
+                b += Gq * s2[O2 + (i3 * NQ + q2) * NQ + tx] + Bq * s2[2 * O2 + (i3 * NQ + q2) * NQ + tx];
+            }
+            s1[(i3 * NI + ty) * NQ + tx] = a;
+            s1[O1 + (i3 * NI + ty) * NQ + tx] = b;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NI && ty < NI) {          // q1 -> i1
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R o = 0;
+#pragma unroll
+            for (int q1 = 0; q1 < NQ; ++q1)
+                o += G[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1] +
+                     B[q1 * NI + tx] * s1[O1 + (i3 * NI + ty) * NQ + q1];
+            out[(i3 * NI + ty) * NI + tx] = o;
+        }
+    }
+    __syncthreads();
+}
+
+// 3D transpose with arbitrary per-direction tables (diagonal assembly):
+// out_i += sum_q f(q) T1(q1,i1) T2(q2,i2) T3(q3,i3).
+template <class C, class R>
+__device__ __forceinline__ void bwd3_tab(const R *__restrict__ T1, const R *__restrict__ T2,
+                                         const R *__restrict__ T3, const R *f, R *s1, R *s2,
+                                         R *out, int tx, int ty, bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ;
+    if (act && tx < NQ && ty < NQ) {
+        R c[NQ];
+#pragma unroll
+        for (int q3 = 0; q3 < NQ; ++q3) c[q3] = f[(q3 * NQ + ty) * NQ + tx];
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R z = 0;
+#pragma unroll
+            for (int q3 = 0; q3 < NQ; ++q3) z += T3[q3 * NI + i3] * c[q3];
+            s2[(i3 * NQ + ty) * NQ + tx] = z;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NQ && ty < NI) {
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R a = 0;
+#pragma unroll
+            for (int q2 = 0; q2 < NQ; ++q2) a += T2[q2 * NI + ty] * s2[(i3 * NQ + q2) * NQ + tx];
+            s1[(i3 * NI + ty) * NQ + tx] = a;
+        }
+    }
+    __syncthreads();
+    if (act && tx < NI && ty < NI) {
+#pragma unroll
+        for (int i3 = 0; i3 < NI; ++i3) {
+            R o = 0;
+#pragma unroll
+            for (int q1 = 0; q1 < NQ; ++q1) o += T1[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1];
+            out[(i3 * NI + ty) * NI + tx] += o;
+        }
+    }
+    __syncthreads();
+}
+
+// 2D: node values u[i2*NI + i1] -> a0 = d/dxbar1, a1 = d/dxbar2, values xv.
+template <class C, class R>
+__device__ __forceinline__ void fwd2(const R *__restrict__ B, const R *__restrict__ G,
+                                     const R *u, R *s1, R *a0, R *a1, R *xv, int tx, int ty,
+                                     bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ, O1 = NI * NQ;
+    if (act && tx < NQ && ty < NI) {
+        R b = 0, g = 0;
+#pragma unroll
+        for (int i1 = 0; i1 < NI; ++i1) {
+            const R v = u[ty * NI + i1];
+            b += B[tx * NI + i1] * v;
+            g += G[tx * NI + i1] * v;
+        }
+        s1[ty * NQ + tx] = b;
+        s1[O1 + ty * NQ + tx] = g;
+    }
+    __syncthreads();
+    if (act && tx < NQ && ty < NQ) {
+        R r0 = 0, r1 = 0, rx = 0;
+#pragma unroll
+        for (int i2 = 0; i2 < NI; ++i2) {
+            const R Bq = B[ty * NI + i2], Gq = G[ty * NI + i2];
+            const R sb = s1[i2 * NQ + tx], sg = s1[O1 + i2 * NQ + tx];
+            r0 += Bq * sg;
+            r1 += Gq * sb;
+            rx += Bq * sb;
+        }
+        const int q = ty * NQ + tx;
+        a0[q] = r0;
+        a1[q] = r1;
+        if (xv) xv[q] = rx;
+    }
+    __syncthreads();
+}
+
+template <class C, class R>
+__device__ __forceinline__ void bwd2(const R *__restrict__ B, const R *__restrict__ G,
+                                     const R *y0, const R *y1, R *s1, R *out, int tx, int ty,
+                                     bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ, O1 = NI * NQ;
+    if (act && tx < NQ && ty < NI) {
+        R a = 0, b = 0;
+#pragma unroll
+        for (int q2 = 0; q2 < NQ; ++q2) {
+            a += B[q2 * NI + ty] * y0[q2 * NQ + tx];
+            b += G[q2 * NI + ty] * y1[q2 * NQ + tx];
+        }
+        s1[ty * NQ + tx] = a;
+        s1[O1 + ty * NQ + tx] = b;
+    }
+    __syncthreads();
+    if (act && tx < NI && ty < NI) {
+        R o = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < NQ; ++q1)
+            o += G[q1 * NI + tx] * s1[ty * NQ + q1] + B[q1 * NI + tx] * s1[O1 + ty * NQ + q1];
+        out[ty * NI + tx] = o;
+    }
+    __syncthreads();
+}
+
+template <class C, class R>
+__device__ __forceinline__ void bwd2_tab(const R *__restrict__ T1, const R *__restrict__ T2,
+                                         const R *f, R *s1, R *out, int tx, int ty, bool act)
+{
+    constexpr int NI = C::NI, NQ = C::NQ;
+    if (act && tx < NQ && ty < NI) {
+        R a = 0;
+#pragma unroll
+        for (int q2 = 0; q2 < NQ; ++q2) a += T2[q2 * NI + ty] * f[q2 * NQ + tx];
+        s1[ty * NQ + tx] = a;
+    }
+    __syncthreads();
+    if (act && tx < NI && ty < NI) {
+        R o = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < NQ; ++q1) o += T1[q1 * NI + tx] * s1[ty * NQ + q1];
+        out[ty * NI + tx] += o;
+    }
+    __syncthreads();
+}
+
+// -------------------------------------------------------------------------
+// Quality metrics at one point (paper Sec. 2.2, Sec. 4.1), FP64.
+//
+// mu is a function of the invariants I1 = |T|^2, tau = det T and (3D)
+// I2 = |cof T|^2 (|T^-1|^2 = I2 / tau^2).  With g1 = 2T, gt = cof T and
+// g2 = 2 (I1 T - T T^T T):
+//   dmu/dT       = f1 g1 + ft gt + f2 g2
+//   d2mu/dT2     = f1 2Id + ft d2tau + f2 d2I2 + sum_uv f_uv g_u (x) g_v.
+// -------------------------------------------------------------------------
+struct Inv {
+    double f1, ft, f2;               // first derivatives of mu w.r.t. (I1, tau, I2)
+    double f11, f1t, ftt, f12, f2t;  // second derivatives (f22 = 0 for all metrics)
+};
+
+template <int D>
+__device__ __forceinline__ void cofactor(const double *T, double *Cf)
+{
+    if (D == 2) {
+        Cf[0] = T[3]; Cf[1] = -T[2]; Cf[2] = -T[1]; Cf[3] = T[0];
+    } else {
+        Cf[0] = T[4] * T[8] - T[5] * T[7];
+        Cf[1] = T[5] * T[6] - T[3] * T[8];
+        Cf[2] = T[3] * T[7] - T[4] * T[6];
+        Cf[3] = T[2] * T[7] - T[1] * T[8];
+        Cf[4] = T[0] * T[8] - T[2] * T[6];
+        Cf[5] = T[1] * T[6] - T[0] * T[7];
+        Cf[6] = T[1] * T[5] - T[2] * T[4];
+        Cf[7] = T[2] * T[3] - T[0] * T[5];
+        Cf[8] = T[0] * T[4] - T[1] * T[3];
+    }
+}
+
+// mu and the scalar derivatives for metric id at invariants (I1, tau, I2).
+__device__ __forceinline__ double metric_scalars(int id, double I1, double tau, double I2, Inv &v)
+{
+    v.f1 = v.ft = v.f2 = v.f11 = v.f1t = v.ftt = v.f12 = v.f2t = 0.0;
+    double mu = 0.0;
+    const double it = 1.0 / tau;
+    if (id == MET_2) {
+        mu = 0.5 * I1 * it - 1.0;
+        v.f1 = 0.5 * it;
+        v.ft = -0.5 * I1 * it * it;
+        v.f1t = -0.5 * it * it;
+        v.ftt = I1 * it * it * it;
+    } else if (id == MET_302) {
+        const double it2 = it * it;
+        mu = I1 * I2 * it2 / 9.0 - 1.0;
+        v.f1 = I2 * it2 / 9.0;
+        v.f2 = I1 * it2 / 9.0;
+        v.ft = -2.0 * I1 * I2 * it2 * it / 9.0;
+        v.f12 = it2 / 9.0;
+        v.f1t = -2.0 * I2 * it2 * it / 9.0;
+        v.f2t = -2.0 * I1 * it2 * it / 9.0;
+        v.ftt = 2.0 * I1 * I2 * it2 * it2 / 3.0;
+    } else {
+        if (id == MET_303 || id == MET_303_55) {
+            const double cr = cbrt(tau);
+            const double c = 1.0 / (cr * cr);        // tau^(-2/3)
+            mu += I1 * c / 3.0 - 1.0;
+            v.f1 += c / 3.0;
+            v.ft += -2.0 * I1 * c * it / 9.0;
+            v.f1t += -2.0 * c * it / 9.0;
+            v.ftt += 10.0 * I1 * c * it * it / 27.0;
+        }
+        if (id == MET_55 || id == MET_303_55) {
+            mu += (tau - 1.0) * (tau - 1.0);
+            v.ft += 2.0 * (tau - 1.0);
+            v.ftt += 2.0;
+        }
+    }
+    return mu;
+}
+
+template <int D>
+__device__ __forceinline__ void invariants(const double *T, double &I1, double &tau, double &I2,
+                                           double *Cf)
+{
+    constexpr int DD = D * D;
+    I1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) I1 += T[i] * T[i];
+    cofactor<D>(T, Cf);
+    tau = 0.0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) tau += T[b] * Cf[b];
+    I2 = 0.0;
+    if (D == 3) {
+#pragma unroll
+        for (int i = 0; i < DD; ++i) I2 += Cf[i] * Cf[i];
+    }
+}
+
+// g2 = dI2/dT = 2 (I1 T - T T^T T) (3D only).
+__device__ __forceinline__ void dI2_3(const double *T, double I1, double *g2, double *TtT,
+                                      double *TTt)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0, u = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s += T[k * 3 + i] * T[k * 3 + j];
+                u += T[i * 3 + k] * T[j * 3 + k];
+            }
+            TtT[i * 3 + j] = s;
+            TTt[i * 3 + j] = u;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += T[i * 3 + k] * TtT[k * 3 + j];
+            g2[i * 3 + j] = 2.0 * (I1 * T[i * 3 + j] - s);
+        }
+}
+
+// sign of the permutation (a, c, 3-a-c) for distinct a != c in {0,1,2}
+__device__ __forceinline__ double eps3(int a, int c)
+{
+    const int m = 3 - a - c;
+    return ((a == 0 && c == 1 && m == 2) || (a == 1 && c == 2 && m == 0) || (a == 2 && c == 0 && m == 1))
+               ? 1.0 : -1.0;
+}
+
+// Entry (r, s) = ((a,b), (c,e)) of d2mu/dT2.
+template <int D>
+__device__ __forceinline__ double metric_K_entry(int r, int s, const double *T, const double *Cf,
+                                                 const double *g2, const double *TtT,
+                                                 const double *TTt, double I1, const Inv &v)
+{
+    const int a = r / D, b = r % D, c = s / D, e = s % D;
+    const double g1r = 2.0 * T[r], g1s = 2.0 * T[s];
+    double k = v.f11 * g1r * g1s + v.f1t * (g1r * Cf[s] + Cf[r] * g1s) + v.ftt * Cf[r] * Cf[s];
+    if (r == s) k += 2.0 * v.f1;
+    // d2 tau / dT_ab dT_ce
+    double d2t = 0.0;
+    if (D == 2) {
+        if (a != c && b != e) d2t = (a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0);
+    } else {
+        if (a != c && b != e) d2t = eps3(a, c) * eps3(b, e) * T[(3 - a - c) * 3 + (3 - b - e)];
+    }
+    k += v.ft * d2t;
+    if (D == 3 && (v.f2 != 0.0 || v.f12 != 0.0 || v.f2t != 0.0)) {
+        k += v.f12 * (g1r * g2[s] + g2[r] * g1s) + v.f2t * (g2[r] * Cf[s] + Cf[r] * g2[s]);
+        double d2 = 4.0 * T[r] * T[s];
+        if (r == s) d2 += 2.0 * I1;
+        if (a == c) d2 -= 2.0 * TtT[e * 3 + b];
+        d2 -= 2.0 * T[a * 3 + e] * T[c * 3 + b];
+        if (b == e) d2 -= 2.0 * TTt[a * 3 + c];
+        k += v.f2 * d2;
+    }
+    return k;
+}
+
+// Size field of the size target and the target scale w (W = w I).
+template <int D>
+__device__ __forceinline__ double target_scale(int target, double h0, const double *xq)
+{
+    if (target != TGT_SIZE) return 1.0;
+    const double twopi = 6.283185307179586476925286766559;
+    double s = 0.5;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s *= sin(twopi * xq[k]);
+    s += 1.0;
+    return h0 * (D == 3 ? cbrt(s) : sqrt(s));
+}
+
+// Packed index of (r, s), r <= s, in a row-major upper triangle of size DD.
+template <int DD>
+__host__ __device__ constexpr int pidx(int r, int s)
+{
+    return r * DD - r * (r - 1) / 2 + (s - r);
+}
+
+}  // namespace tmop

@@ -1,0 +1,86 @@
+// Internal declarations shared by the host code and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tmop.h"
+
+namespace tmop {
+
+// Supported (dim, order, nq1d) triples: every p in 1..4 with nq1d in {p+1, p+2}.
+#define TMOP_CONFIGS(X)                                                                    \
+    X(2, 1, 2) X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 4) X(2, 3, 5) X(2, 4, 5) X(2, 4, 6) \
+    X(3, 1, 2) X(3, 1, 3) X(3, 2, 3) X(3, 2, 4) X(3, 3, 4) X(3, 3, 5) X(3, 4, 5) X(3, 4, 6)
+#define TMOP_KEY(d, p, q) ((d) * 100 + (p) * 10 + (q))
+
+struct ElemParams;
+
+// Element-kernel launchers (one translation unit each).  Return the launch
+// error.  nblocks() is the grid size a launch over E elements uses.
+int64_t elem_blocks(int d, int p, int q, int64_t E);
+bool elem_supported(int d, int p, int q);
+cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
+                          cudaStream_t s);
+cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
+                            cudaStream_t s);
+cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double *x, void *H,
+                          int prec, cudaStream_t s);
+cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
+                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s);
+cudaError_t launch_diag(int d, int p, int q, const ElemParams &P, const void *H, void *ev, int prec,
+                        cudaStream_t s);
+
+// Host tables: Gauss-Legendre rule on [0,1], GLL nodes, Lagrange B/G.
+void host_gauss_legendre(int n, double *x, double *w);
+void host_gll_nodes(int n, double *x);
+void host_basis_tables(int ni, int nq, double *B, double *G, double *w1d);
+
+// MINRES scalar state kept on the device.
+struct MinresState {
+    double beta, beta_old, beta1, alpha, dbar, eps, eps_old, phibar, cs, sn, gamma, delta, phi;
+    int stop_iter;   // first iteration after which nothing changes (INT_MAX while running)
+    int breakdown;
+    int iters;
+    int pad;
+};
+
+// Vector / reduction launchers (vec_kernels.cu).
+int reduce_blocks(int64_t n);
+cudaError_t launch_assemble(const void *ev, int ev_prec, const int32_t *ptr, const int32_t *idx,
+                            const uint8_t *fixed, const void *vfix, int mode, int64_t Nx, int D,
+                            int64_t ENP, void *out, int out_prec, const int *stop, int k,
+                            cudaStream_t s);
+cudaError_t launch_mask(const void *v, const uint8_t *fixed, int64_t n, void *out, int prec,
+                        cudaStream_t s);
+cudaError_t launch_trial(const double *x, const double *dx, double alpha, int64_t n, double *out,
+                         cudaStream_t s);
+cudaError_t launch_dot(const void *a, const void *b, int prec, int64_t n, double *part, int nb,
+                       cudaStream_t s);
+cudaError_t launch_finalize_sum(const double *part, int nb, double *out, cudaStream_t s);
+cudaError_t launch_finalize_energy(const double *part, int64_t nb, double *out, cudaStream_t s);
+cudaError_t launch_jacobi(const void *diag, int prec, int64_t n, void *minv, cudaStream_t s);
+cudaError_t launch_minres_init(const double *b, const void *minv, int prec, int64_t n, void *r1,
+                               void *r2, void *y, double *part, int nb, cudaStream_t s);
+cudaError_t launch_minres_start(const double *part, int nb, MinresState *st, int max_it,
+                                cudaStream_t s);
+cudaError_t launch_minres_scale(const void *y, const MinresState *st, int prec, int64_t n, void *v,
+                                cudaStream_t s);
+cudaError_t launch_lanczos_a(void *z, const void *r1, const void *v, const MinresState *st,
+                             int prec, int64_t n, int k, double *part, int nb, cudaStream_t s);
+cudaError_t launch_fin_alpha(const double *part, int nb, MinresState *st, int k, cudaStream_t s);
+cudaError_t launch_lanczos_b(void *y, const void *r2, const void *minv, const MinresState *st,
+                             int prec, int64_t n, int k, void *ynew, double *part, int nb,
+                             cudaStream_t s);
+cudaError_t launch_fin_beta(const double *part, int nb, MinresState *st, int k, double rtol,
+                            int fixed_its, cudaStream_t s);
+cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *wnew, double *dx,
+                                 const void *ynew, const MinresState *st, int prec, int64_t n,
+                                 int k, cudaStream_t s);
+
+// Global launch counter (instrumentation).
+void count_launch(int n = 1);
+
+}  // namespace tmop

@@ -1,0 +1,466 @@
+// Vector kernels of the TMOP Newton step: deterministic assembly of element
+// vectors through the transposed element map, fixed-DOF masks, FP64
+// reductions with fixed block order, and the fused Jacobi-preconditioned
+// MINRES updates (Paige & Saunders 1975, the inner solver of paper Sec. 2.3
+// and 3.4) whose scalar recurrences run in one-thread kernels so that the
+// host never has to read them inside an iteration.
+#include <climits>
+#include <cmath>
+
+#include "tmop_internal.h"
+
+namespace tmop {
+
+namespace {
+
+constexpr int VT = 256;           // threads per block of the vector kernels
+constexpr int RED_MAX = 1184;     // 8 CTAs per SM on 148 SMs
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;   // valid on thread 0
+}
+
+template <class R>
+__device__ __forceinline__ bool skip(const MinresState *st, int k)
+{
+    return st->stop_iter < k;
+}
+
+// y[dof] = sum over the element entries of the node (fixed order), then the
+// fixed-DOF rule: mode 0 -> 0, mode 1 -> vfix[dof] (or 0), mode 2 -> 1.
+template <class RI, class RO>
+__global__ void k_assemble(const RI *__restrict__ ev, const int32_t *__restrict__ ptr,
+                           const int32_t *__restrict__ idx, const uint8_t *__restrict__ fixed,
+                           const RO *__restrict__ vfix, int mode, int64_t Nx, int D, int64_t ENP,
+                           RO *__restrict__ out, const int *__restrict__ stop, int k)
+{
+    if (stop && *stop < k) return;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nx) return;
+    const int b = ptr[n], e = ptr[n + 1];
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        for (int j = b; j < e; ++j) s += (double)ev[a * ENP + idx[j]];
+        const int64_t dof = a * Nx + n;
+        if (fixed && fixed[dof]) s = (mode == 0) ? 0.0 : (mode == 1 ? (vfix ? (double)vfix[dof] : 0.0) : 1.0);
+        out[dof] = (RO)s;
+    }
+}
+
+template <class R>
+__global__ void k_mask(const R *__restrict__ v, const uint8_t *__restrict__ fixed, int64_t n,
+                       R *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (fixed && fixed[i]) ? R(0) : v[i];
+}
+
+__global__ void k_trial(const double *__restrict__ x, const double *__restrict__ dx, double alpha,
+                        int64_t n, double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] - alpha * dx[i];
+}
+
+template <class R>
+__global__ void k_dot(const R *__restrict__ a, const R *__restrict__ b, int64_t n,
+                      double *__restrict__ part)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_finalize_sum(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// part holds (sum, min) pairs; out = (sum, min).
+__global__ void k_finalize_energy(const double *__restrict__ part, int64_t nb, double *__restrict__ out)
+{
+    __shared__ double sh[VT / 32], shm[VT / 32];
+    double s = 0.0, m = INFINITY;
+    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+        s += part[2 * i];
+        m = fmin(m, part[2 * i + 1]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) shm[wid] = m;
+    s = block_sum(s, sh);     // contains a __syncthreads, publishing shm
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, shm[i]);
+        out[0] = s;
+        out[1] = m;
+    }
+}
+
+template <class R>
+__global__ void k_jacobi(const R *__restrict__ diag, int64_t n, R *__restrict__ minv)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs((double)diag[i]);
+        minv[i] = (R)(a < 1e-300 ? 1.0 : 1.0 / a);
+    }
+}
+
+// ---------------------------------------------------------------- MINRES
+// r1 = r2 = b, y = M^-1 b; partial dot(b, y).
+template <class R>
+__global__ void k_minres_init(const double *__restrict__ b, const R *__restrict__ minv, int64_t n,
+                              R *__restrict__ r1, R *__restrict__ r2, R *__restrict__ y,
+                              double *__restrict__ part)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R bi = (R)b[i];
+        const R yi = minv[i] * bi;
+        r1[i] = bi;
+        r2[i] = bi;
+        y[i] = yi;
+        s += (double)bi * (double)yi;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_minres_start(const double *__restrict__ part, int nb, MinresState *st)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double b1 = sqrt(fmax(s, 0.0));
+        st->beta1 = b1;
+        st->beta = b1;
+        st->beta_old = 0.0;
+        st->alpha = 0.0;
+        st->dbar = 0.0;
+        st->eps = 0.0;
+        st->eps_old = 0.0;
+        st->phibar = b1;
+        st->cs = -1.0;
+        st->sn = 0.0;
+        st->gamma = 1.0;
+        st->delta = 0.0;
+        st->phi = 0.0;
+        st->stop_iter = (b1 > 0.0) ? INT_MAX : 0;
+        st->breakdown = 0;
+        st->iters = 0;
+    }
+}
+
+// v = y / beta (first Lanczos vector).
+template <class R>
+__global__ void k_minres_scale(const R *__restrict__ y, const MinresState *__restrict__ st, int64_t n,
+                               R *__restrict__ v)
+{
+    if (st->stop_iter < 1) return;
+    const double ib = 1.0 / st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (R)((double)y[i] * ib);
+}
+
+// y = z - (beta/beta_old) r1 (k >= 2), in place in z; partial dot(v, y).
+template <class R>
+__global__ void k_lanczos_a(R *__restrict__ z, const R *__restrict__ r1, const R *__restrict__ v,
+                            const MinresState *__restrict__ st, int64_t n, int k,
+                            double *__restrict__ part)
+{
+    if (st->stop_iter < k) return;
+    __shared__ double sh[VT / 32];
+    const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R yi = (R)((double)z[i] - c * (double)r1[i]);
+        z[i] = yi;
+        s += (double)v[i] * (double)yi;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_fin_alpha(const double *__restrict__ part, int nb, MinresState *st, int k)
+{
+    if (st->stop_iter < k) return;
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) st->alpha = s;
+}
+
+// y -= (alpha/beta) r2 (in place); ynew = M^-1 y; partial dot(y, ynew).
+template <class R>
+__global__ void k_lanczos_b(R *__restrict__ y, const R *__restrict__ r2, const R *__restrict__ minv,
+                            const MinresState *__restrict__ st, int64_t n, int k,
+                            R *__restrict__ ynew, double *__restrict__ part)
+{
+    if (st->stop_iter < k) return;
+    __shared__ double sh[VT / 32];
+    const double c = st->alpha / st->beta;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R yi = (R)((double)y[i] - c * (double)r2[i]);
+        const R zi = minv[i] * yi;
+        y[i] = yi;
+        ynew[i] = zi;
+        s += (double)yi * (double)zi;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// beta_{k+1}, the Givens rotations of the tridiagonal QR, phi and the stop test.
+__global__ void k_fin_beta(const double *__restrict__ part, int nb, MinresState *st, int k,
+                           double rtol, int fixed_its)
+{
+    if (st->stop_iter < k) return;
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    st->iters = k;
+    if (s < 0.0) {                       // M^-1 not positive: cannot happen with |diag|
+        st->breakdown = 1;
+        st->stop_iter = k - 1;           // discard this iteration
+        return;
+    }
+    st->beta_old = st->beta;
+    const double beta = sqrt(s);
+    st->beta = beta;
+    const double alpha = st->alpha;
+    st->eps_old = st->eps;
+    const double delta = st->cs * st->dbar + st->sn * alpha;
+    const double gbar = st->sn * st->dbar - st->cs * alpha;
+    st->eps = st->sn * beta;
+    st->dbar = -st->cs * beta;
+    double gamma = sqrt(gbar * gbar + beta * beta);
+    if (gamma < 1e-300) gamma = 1e-300;
+    st->gamma = gamma;
+    st->delta = delta;
+    st->cs = gbar / gamma;
+    st->sn = beta / gamma;
+    st->phi = st->cs * st->phibar;
+    st->phibar = st->sn * st->phibar;
+    if ((!fixed_its && st->phibar <= rtol * st->beta1) || beta == 0.0) st->stop_iter = k;
+}
+
+// wnew = (v - eps_old w1 - delta w2) / gamma; dx += phi wnew; v = ynew / beta.
+template <class R>
+__global__ void k_minres_update(R *__restrict__ v, const R *__restrict__ w1, const R *__restrict__ w2,
+                                R *__restrict__ wnew, double *__restrict__ dx,
+                                const R *__restrict__ ynew, const MinresState *__restrict__ st,
+                                int64_t n, int k)
+{
+    if (st->stop_iter < k) return;
+    const double eo = st->eps_old, de = st->delta, ig = 1.0 / st->gamma, ph = st->phi;
+    const double ib = (st->beta > 0.0) ? 1.0 / st->beta : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wn = ((double)v[i] - eo * (double)w1[i] - de * (double)w2[i]) * ig;
+        wnew[i] = (R)wn;
+        dx[i] += ph * wn;
+        v[i] = (R)((double)ynew[i] * ib);
+    }
+}
+
+inline unsigned grid_for(int64_t n)
+{
+    int64_t g = (n + VT - 1) / VT;
+    if (g > RED_MAX) g = RED_MAX;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int reduce_blocks(int64_t n) { return (int)grid_for(n); }
+
+cudaError_t launch_assemble(const void *ev, int ev_prec, const int32_t *ptr, const int32_t *idx,
+                            const uint8_t *fixed, const void *vfix, int mode, int64_t Nx, int D,
+                            int64_t ENP, void *out, int out_prec, const int *stop, int k,
+                            cudaStream_t s)
+{
+    if (Nx == 0) return cudaSuccess;
+    const unsigned g = (unsigned)((Nx + VT - 1) / VT);
+    if (ev_prec == TMOP_FP64 && out_prec == TMOP_FP64)
+        k_assemble<double, double><<<g, VT, 0, s>>>((const double *)ev, ptr, idx, fixed,
+                                                    (const double *)vfix, mode, Nx, D, ENP,
+                                                    (double *)out, stop, k);
+    else if (ev_prec == TMOP_FP32 && out_prec == TMOP_FP32)
+        k_assemble<float, float><<<g, VT, 0, s>>>((const float *)ev, ptr, idx, fixed,
+                                                  (const float *)vfix, mode, Nx, D, ENP,
+                                                  (float *)out, stop, k);
+    else
+        return cudaErrorInvalidValue;
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask(const void *v, const uint8_t *fixed, int64_t n, void *out, int prec,
+                        cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (prec == TMOP_FP32)
+        k_mask<float><<<grid_for(n), VT, 0, s>>>((const float *)v, fixed, n, (float *)out);
+    else
+        k_mask<double><<<grid_for(n), VT, 0, s>>>((const double *)v, fixed, n, (double *)out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trial(const double *x, const double *dx, double alpha, int64_t n, double *out,
+                         cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_trial<<<grid_for(n), VT, 0, s>>>(x, dx, alpha, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const void *a, const void *b, int prec, int64_t n, double *part, int nb,
+                       cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_dot<float><<<nb, VT, 0, s>>>((const float *)a, (const float *)b, n, part);
+    else
+        k_dot<double><<<nb, VT, 0, s>>>((const double *)a, (const double *)b, n, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_sum(const double *part, int nb, double *out, cudaStream_t s)
+{
+    k_finalize_sum<<<1, VT, 0, s>>>(part, nb, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_energy(const double *part, int64_t nb, double *out, cudaStream_t s)
+{
+    k_finalize_energy<<<1, VT, 0, s>>>(part, nb, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const void *diag, int prec, int64_t n, void *minv, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (prec == TMOP_FP32)
+        k_jacobi<float><<<grid_for(n), VT, 0, s>>>((const float *)diag, n, (float *)minv);
+    else
+        k_jacobi<double><<<grid_for(n), VT, 0, s>>>((const double *)diag, n, (double *)minv);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_init(const double *b, const void *minv, int prec, int64_t n, void *r1,
+                               void *r2, void *y, double *part, int nb, cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_minres_init<float><<<nb, VT, 0, s>>>(b, (const float *)minv, n, (float *)r1, (float *)r2,
+                                              (float *)y, part);
+    else
+        k_minres_init<double><<<nb, VT, 0, s>>>(b, (const double *)minv, n, (double *)r1,
+                                               (double *)r2, (double *)y, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_start(const double *part, int nb, MinresState *st, int, cudaStream_t s)
+{
+    k_minres_start<<<1, VT, 0, s>>>(part, nb, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_scale(const void *y, const MinresState *st, int prec, int64_t n, void *v,
+                                cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_minres_scale<float><<<grid_for(n), VT, 0, s>>>((const float *)y, st, n, (float *)v);
+    else
+        k_minres_scale<double><<<grid_for(n), VT, 0, s>>>((const double *)y, st, n, (double *)v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_a(void *z, const void *r1, const void *v, const MinresState *st,
+                             int prec, int64_t n, int k, double *part, int nb, cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_lanczos_a<float><<<nb, VT, 0, s>>>((float *)z, (const float *)r1, (const float *)v, st, n,
+                                            k, part);
+    else
+        k_lanczos_a<double><<<nb, VT, 0, s>>>((double *)z, (const double *)r1, (const double *)v,
+                                             st, n, k, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin_alpha(const double *part, int nb, MinresState *st, int k, cudaStream_t s)
+{
+    k_fin_alpha<<<1, VT, 0, s>>>(part, nb, st, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_b(void *y, const void *r2, const void *minv, const MinresState *st,
+                             int prec, int64_t n, int k, void *ynew, double *part, int nb,
+                             cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_lanczos_b<float><<<nb, VT, 0, s>>>((float *)y, (const float *)r2, (const float *)minv, st,
+                                            n, k, (float *)ynew, part);
+    else
+        k_lanczos_b<double><<<nb, VT, 0, s>>>((double *)y, (const double *)r2,
+                                             (const double *)minv, st, n, k, (double *)ynew, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin_beta(const double *part, int nb, MinresState *st, int k, double rtol,
+                            int fixed_its, cudaStream_t s)
+{
+    k_fin_beta<<<1, VT, 0, s>>>(part, nb, st, k, rtol, fixed_its);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *wnew, double *dx,
+                                 const void *ynew, const MinresState *st, int prec, int64_t n,
+                                 int k, cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_minres_update<float><<<grid_for(n), VT, 0, s>>>((float *)v, (const float *)w1,
+                                                         (const float *)w2, (float *)wnew, dx,
+                                                         (const float *)ynew, st, n, k);
+    else
+        k_minres_update<double><<<grid_for(n), VT, 0, s>>>((double *)v, (const double *)w1,
+                                                          (const double *)w2, (double *)wnew, dx,
+                                                          (const double *)ynew, st, n, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tmop
