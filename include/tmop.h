@@ -177,6 +177,35 @@ tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag);
 tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *opts,
                              tmop_step_report *rep);
 
+/* Energy and min det(A) without allocating anything (the paper has no
+ * counterpart: this exists for callers of this library that cannot call
+ * cudaMalloc, e.g. code running inside an application whose memory pool has
+ * claimed the device memory, or latency-bound loops where cudaMalloc/cudaFree
+ * would synchronise the device).  It computes what tmop_energy computes, with
+ * no context: the per-CTA partial sums and the 1D basis tables live in one
+ * file-scope device array of 1 MiB (65,536 partial pairs + 128 table
+ * values), which every GPU that loads the library holds until the process
+ * exits.
+ *   desc          host; sizes, metric and target as for tmop_setup
+ *                 (hess_precision is ignored).
+ *   elem_to_node  device int32, num_elems * (order+1)^dim, in range (not checked).
+ *   x             device FP64, dim * num_nodes.
+ *   out           device FP64[2]; receives F(x) and min det(A).  F is the sum
+ *                 over points with det A > 0: check out[1] > 0 (otherwise the
+ *                 mesh is inverted and F is meaningless).
+ *   cuda_stream   stream for the copy and the two launches.
+ * Meshes needing more than 65,536 CTAs (e.g. more than 524,288 elements for
+ * 3D p = 3 with 4^3 points) are rejected with TMOP_ERR_ARG; use tmop_energy.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * every value a call reads is written by that call, so nothing is cleared.
+ * Calls that overlap on the GPU (different streams, or different host
+ * threads) race on the array.  Asynchronous; never calls cudaMalloc,
+ * cudaFree or any allocating routine. */
+tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t *elem_to_node,
+                                const double *x, double *out, void *cuda_stream);
+
 /* Free the context and everything it owns.  NULL is accepted. */
 void tmop_destroy(tmop_ctx *ctx);
 

@@ -25,7 +25,7 @@ K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)
 EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_hessian_apply", "tmop_hessian_diag", "tmop_newton_step", "tmop_destroy",
            "tmop_status_string", "tmop_last_error", "tmop_launch_count", "tmop_profile_enable",
-           "tmop_profile_read", "tmop_device_bytes")
+           "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc")
 
 
 class TmopError(RuntimeError):
@@ -85,6 +85,7 @@ def lib():
             "tmop_profile_enable": (I, [P, I]),
             "tmop_profile_read": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]),
             "tmop_device_bytes": (I64, [P]),
+            "tmop_energy_noalloc": (I, [ctypes.POINTER(Desc), P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -184,3 +185,15 @@ def tmop_profile_read(ctx: int, kernel_class: int):
 
 def tmop_device_bytes(ctx: int) -> int:
     return lib().tmop_device_bytes(ctx)
+
+
+def tmop_energy_noalloc(desc: Desc, elem_to_node, x, out, stream=None):
+    """Energy and min det into the device array ``out`` (2 float64) with no
+    allocation by the library.  Returns the status (no exception)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    return lib().tmop_energy_noalloc(ctypes.byref(desc), _ptr(elem_to_node), _ptr(x), _ptr(out),
+                                     stream)

@@ -53,6 +53,7 @@ struct ProfRec {
 
 namespace tmop {
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_last_error(const std::string &msg) { g_last_error = msg; }
 }  // namespace tmop
 
 struct tmop_ctx {

@@ -1,0 +1,111 @@
+// tmop_energy_noalloc: the energy / min det(A) computation for callers that
+// must not allocate device memory.  It runs the same energy kernel and final
+// reduction as tmop_energy, but its scratch (per-CTA partial sums and the 1D
+// basis tables) lives in one file-scope device array instead of memory a
+// context allocates.
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "tmop_device.cuh"
+#include "tmop_internal.h"
+
+namespace {
+
+constexpr int kMaxCtas = 65536;                   // partial (sum, min) pairs
+constexpr int kTableOffset = 2 * kMaxCtas;        // 1D tables follow the partials
+constexpr int kTableMax = 128;                    // >= 2 nq (p+1) + nq for p <= 4, nq <= 6
+constexpr int kScratchDoubles = kTableOffset + kTableMax;
+
+// Shared by every call in the process on this device; holds the last call's
+// contents until the library is unloaded.
+static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double *g_scratch_addr[kMaxDevices] = {nullptr};
+
+tmop_status set_error(tmop_status st, const std::string &m)
+{
+    tmop::set_last_error(m);
+    return st;
+}
+
+// Device address of the scratch array for the current device (looked up once
+// per device; host code cannot use the symbol itself as a device pointer).
+tmop_status scratch_for_current_device(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(TMOP_ERR_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return set_error(TMOP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_scratch_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return TMOP_OK;
+}
+
+}  // namespace
+
+extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t *elem_to_node,
+                                           const double *x, double *out, void *cuda_stream)
+{
+    using namespace tmop;
+    if (!desc || !x || !out) return set_error(TMOP_ERR_ARG, "desc, x and out must not be NULL");
+    const tmop_desc &D = *desc;
+    if (D.dim != 2 && D.dim != 3) return set_error(TMOP_ERR_ARG, "dim must be 2 or 3");
+    if (!elem_supported(D.dim, D.order, D.nq1d))
+        return set_error(TMOP_ERR_UNSUPPORTED, "order must be 1..4 and nq1d order+1 or order+2");
+    const bool metric_ok = (D.metric == TMOP_METRIC_2 && D.dim == 2) ||
+                           ((D.metric == TMOP_METRIC_302 || D.metric == TMOP_METRIC_303 ||
+                             D.metric == TMOP_METRIC_303_55) && D.dim == 3) ||
+                           D.metric == TMOP_METRIC_55;
+    if (!metric_ok) return set_error(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
+    if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
+        return set_error(TMOP_ERR_ARG, "unknown target");
+    if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
+        return set_error(TMOP_ERR_ARG, "target_h0 must be > 0");
+    if (D.num_elems < 0 || D.num_nodes <= 0) return set_error(TMOP_ERR_ARG, "bad mesh sizes");
+    if (D.num_elems > 0 && !elem_to_node) return set_error(TMOP_ERR_ARG, "elem_to_node is NULL");
+    const int64_t nb = elem_blocks(D.dim, D.order, D.nq1d, D.num_elems);
+    if (nb > kMaxCtas)
+        return set_error(TMOP_ERR_ARG, "mesh too large for tmop_energy_noalloc: needs " +
+                                           std::to_string(nb) + " CTAs, the static scratch holds " +
+                                           std::to_string(kMaxCtas) + "; use tmop_energy");
+
+    double *scratch = nullptr;
+    tmop_status st = scratch_for_current_device(&scratch);
+    if (st != TMOP_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    // 1D tables on the host stack, copied into the scratch array
+    const int ni = D.order + 1, nq = D.nq1d;
+    double tab[kTableMax];
+    host_basis_tables(ni, nq, tab, tab + nq * ni, tab + 2 * nq * ni);
+    const int tabn = 2 * nq * ni + nq;
+    cudaError_t e = cudaMemcpyAsync(scratch + kTableOffset, tab, sizeof(double) * tabn,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("table copy: ") + cudaGetErrorString(e));
+
+    ElemParams P;
+    P.map = elem_to_node;
+    P.E = D.num_elems;
+    P.Nx = D.num_nodes;
+    P.tab = scratch + kTableOffset;
+    P.tabf = nullptr;
+    P.metric = D.metric;
+    P.target = D.target;
+    P.h0 = D.target_h0;
+    // every partial slot the reduction reads is written by this launch, so
+    // nothing in the scratch needs clearing first
+    e = launch_energy(D.dim, D.order, D.nq1d, P, x, scratch, s);
+    if (e == cudaSuccess) e = launch_finalize_energy(scratch, nb, out, s);
+    if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("energy launch: ") + cudaGetErrorString(e));
+    return TMOP_OK;
+}

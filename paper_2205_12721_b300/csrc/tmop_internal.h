@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/tmop.h"
@@ -82,5 +83,8 @@ cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *
 
 // Global launch counter (instrumentation).
 void count_launch(int n = 1);
+
+// Text returned by tmop_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
 
 }  // namespace tmop
