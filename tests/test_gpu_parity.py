@@ -153,6 +153,7 @@ def _newton_parity(m, metric, steps, target=0, h0=1.0, nq=None, max_it=200):
     gm = gpu_mesh(m, metric, nq, target, h0)
     xo = m.x.copy()
     xg = dev(m.x)
+    g_first = None
     for k in range(steps):
         x_start = host(xg)
         xs = x_start.copy()
@@ -160,6 +161,9 @@ def _newton_parity(m, metric, steps, target=0, h0=1.0, nq=None, max_it=200):
         ro = O.newton_step(om, xs, 1e-8, max_it)
         rg = gm.newton_step(xg, 1e-8, max_it)
         assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
+        g_first = g_first or ro["grad_norm"]
+        if ro["grad_norm"] < 1e-8 * g_first:
+            break        # converged: F is at rounding level, line-search tests are ties
         assert ro["minres_iters"] < max_it, "case must be well conditioned (MINRES converges)"
         assert rg["halvings"] == ro["halvings"], (k, ro, rg)
         assert abs(rg["minres_iters"] - ro["minres_iters"]) <= 1, (k, ro, rg)
@@ -167,7 +171,7 @@ def _newton_parity(m, metric, steps, target=0, h0=1.0, nq=None, max_it=200):
         err = np.abs(host(xg) - xs).max()
         assert err <= 1e-10 * m.h, (k, err)
         O.newton_step(om, xo, 1e-8, max_it)             # the oracle's own trajectory
-    assert np.abs(host(xg) - xo).max() <= 1e-10 * m.h
+        assert np.abs(host(xg) - xo).max() <= 1e-10 * m.h
     gm.close()
     return xo
 
