@@ -40,7 +40,7 @@ MINRES_ITS = 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_apply launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {"fp64": 2.779e9, "fp32": None}
+TRAFFIC_BYTES = {"fp64-native": 2.779e9}
 
 
 def flops_apply_per_elem(d, ni, nq, ns):
@@ -216,26 +216,30 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     gbs = byts / (apply_avg_ms * 1e-3) / 1e9
-    if args.precision == "fp64":
+    if args.precision == "fp64-native":
         ach = flops / (apply_avg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": args.traffic,
                 "peak_source": "nominal FP64 rate of the profiling recipe",
-                "kernel": "k_apply<Cfg<3,3,4>,double>", "flops_per_launch": flops,
+                "kernel": "k_apply<Cfg<3,3,4>,double,double>", "flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm,
                              "frac": (gbs / hbm) if hbm else None, "bytes_per_launch": byts}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (gbs / hbm) if hbm else None, "traffic": args.traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "kernel": "k_apply<Cfg<3,3,4>,float>", "bytes_per_launch": byts}
+                "kernel": ("k_apply<Cfg<3,3,4>,float,float>" if args.precision == "fp32"
+                           else "k_apply<Cfg<3,3,4>,double,df> (double-float)"),
+                "bytes_per_launch": byts,
+                "flops_view": {"fp64_equiv_tflops": flops / (apply_avg_ms * 1e-3) / 1e12}}
     roof["avg_launch_ms"] = apply_avg_ms
     roof["launches"] = apply_n
     roof["apply_gdofs"] = m.ndof / (apply_avg_ms * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 (H, MINRES) / f64",
+        "vs_baseline": None, "dtype": {"fp64": "f64 (double-float contractions)", "fp64-native": "f64",
+                  "fp32": "f32 (H, MINRES) / f64"}[args.precision],
         "data": "synthetic seeded perturbed Cartesian mesh (no dataset)",
         "config": {"workload": f"3D hex {m.n[0]}^3 Q{p}, {nq}^3 Gauss pts, mu_303, identity target, "
                                f"1 Newton step = energy+grad+PA setup+diag+{MINRES_ITS} MINRES+line search",
@@ -305,7 +309,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp64-native"])
     ap.add_argument("--n-e", dest="n_e", type=int, default=48)
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--cpu-sample-n", dest="cpu_sample_n", type=int, default=8)

@@ -72,8 +72,16 @@ enum { TMOP_TARGET_IDENTITY = 0, TMOP_TARGET_SIZE_FIELD = 1 };
 
 /* Precision of the stored d2mu/dT2 data, the Hessian action, its diagonal
  * and the inner MINRES vectors.  Energy, gradient, det(A), the line search
- * and the outer convergence test are always FP64. */
-enum { TMOP_FP64 = 0, TMOP_FP32 = 1 };
+ * and the outer convergence test always have FP64 inputs, outputs and
+ * accuracy.
+ *   TMOP_FP64         FP64 vectors; contractions and stored data in
+ *                     double-float pairs on the FP32 units (48-bit
+ *                     significand, relative rounding ~4e-15), because B300
+ *                     issues FP64 arithmetic ~60x slower than FP32.
+ *   TMOP_FP32         FP32 stored data, action, diagonal and Krylov vectors;
+ *                     energy/gradient/setup contractions in double-float.
+ *   TMOP_FP64_NATIVE  every contraction on the FP64 units (reference path). */
+enum { TMOP_FP64 = 0, TMOP_FP32 = 1, TMOP_FP64_NATIVE = 2 };
 
 typedef struct {
     int dim;             /* 2 or 3 */
@@ -84,7 +92,7 @@ typedef struct {
     int metric;          /* TMOP_METRIC_* valid for dim */
     int target;          /* TMOP_TARGET_* */
     double target_h0;    /* h0 of the size target (ignored for IDENTITY) */
-    int hess_precision;  /* TMOP_FP64 or TMOP_FP32 */
+    int hess_precision;  /* TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE */
 } tmop_desc;
 
 typedef struct {
@@ -152,14 +160,14 @@ tmop_status tmop_hessian_setup(tmop_ctx *ctx, const double *x);
  * forward contractions B G v, pointwise H : dA, transposed contractions,
  * deterministic assembly.  Fixed DOFs: v is treated as zero there on input
  * and y = v there on output.
- *   v, y  device, dim * num_nodes, double* for TMOP_FP64 contexts and
- *         float* for TMOP_FP32 contexts; must not alias.
+ *   v, y  device, dim * num_nodes, double* for TMOP_FP64 / TMOP_FP64_NATIVE
+ *         contexts and float* for TMOP_FP32 contexts; must not alias.
  * Requires a previous tmop_hessian_setup.  Asynchronous. */
 tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y);
 
 /* Diagonal of d2F from the stored data by tensor contractions (Sec. 3.4,
  * Jacobi preconditioning); 1 on fixed DOFs.
- *   diag  device, dim * num_nodes, double* (FP64 context) or float* (FP32).
+ *   diag  device, dim * num_nodes, double* (FP64 contexts) or float* (FP32).
  * Requires a previous tmop_hessian_setup.  Asynchronous. */
 tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag);
 
@@ -183,11 +191,11 @@ tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *o
  * claimed the device memory, or latency-bound loops where cudaMalloc/cudaFree
  * would synchronise the device).  It computes what tmop_energy computes, with
  * no context: the per-CTA partial sums and the 1D basis tables live in one
- * file-scope device array of 1 MiB (65,536 partial pairs + 128 table
+ * file-scope device array of 1 MiB (65,536 partial pairs + 2 x 128 table
  * values), which every GPU that loads the library holds until the process
  * exits.
- *   desc          host; sizes, metric and target as for tmop_setup
- *                 (hess_precision is ignored).
+ *   desc          host; sizes, metric and target as for tmop_setup;
+ *                 hess_precision selects the contraction arithmetic as there.
  *   elem_to_node  device int32, num_elems * (order+1)^dim, in range (not checked).
  *   x             device FP64, dim * num_nodes.
  *   out           device FP64[2]; receives F(x) and min det(A).  F is the sum

@@ -59,6 +59,8 @@ void set_last_error(const std::string &msg) { g_last_error = msg; }
 struct tmop_ctx {
     tmop_desc desc{};
     int d = 0, p = 0, nq = 0, ni = 0, np = 0, nqd = 0, ns = 0, prec = 0;
+    int vprec = 0;               // vector type of the action / MINRES: FP32 or FP64
+    int arith = 0;               // ARITH_DW or ARITH_NATIVE for energy/gradient/setup
     int64_t E = 0, Nx = 0, ndof = 0, ENP = 0;
     size_t rsz = 8;
     cudaStream_t stream = nullptr;
@@ -67,6 +69,7 @@ struct tmop_ctx {
     uint8_t *fixed = nullptr;
     double *tab = nullptr;
     float *tabf = nullptr;
+    df *tabw = nullptr;
     // partial assembly data and element vectors
     void *H = nullptr;
     bool h_ready = false;
@@ -100,6 +103,7 @@ struct tmop_ctx {
         P.Nx = Nx;
         P.tab = tab;
         P.tabf = tabf;
+        P.tabw = tabw;
         P.metric = desc.metric;
         P.target = desc.target;
         P.h0 = desc.target_h0;
@@ -193,7 +197,7 @@ tmop_status energy_async(tmop_ctx *c, const double *x)
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
     TRY(timed(c, TMOP_K_ENERGY, "energy kernel",
-              [&] { return launch_energy(c->d, c->p, c->nq, P, x, c->part, c->stream); }));
+              [&] { return launch_energy(c->d, c->p, c->nq, P, x, c->part, c->arith, c->stream); }));
     CK(launch_finalize_energy(c->part, nb, c->scal, c->stream));
     return TMOP_OK;
 }
@@ -222,7 +226,7 @@ tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
 {
     const ElemParams P = c->params();
     TRY(timed(c, TMOP_K_GRADIENT, "gradient kernel",
-              [&] { return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->stream); }));
+              [&] { return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->arith, c->stream); }));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 0,
                                c->Nx, c->d, c->ENP, g, TMOP_FP64, nullptr, 0, c->stream);
@@ -259,8 +263,8 @@ tmop_status apply_internal(tmop_ctx *c, const void *v, void *y, const int *stop,
         return launch_apply(c->d, c->p, c->nq, P, v, c->H, c->evR, c->prec, stop, k, c->stream);
     }));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
-        return launch_assemble(c->evR, c->prec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
-                               c->Nx, c->d, c->ENP, y, c->prec, stop, k, c->stream);
+        return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
+                               c->Nx, c->d, c->ENP, y, c->vprec, stop, k, c->stream);
     }));
     return TMOP_OK;
 }
@@ -272,8 +276,8 @@ tmop_status diag_async(tmop_ctx *c, void *diag)
         return launch_diag(c->d, c->p, c->nq, P, c->H, c->evR, c->prec, c->stream);
     }));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
-        return launch_assemble(c->evR, c->prec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 2,
-                               c->Nx, c->d, c->ENP, diag, c->prec, nullptr, 0, c->stream);
+        return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 2,
+                               c->Nx, c->d, c->ENP, diag, c->vprec, nullptr, 0, c->stream);
     }));
     return TMOP_OK;
 }
@@ -283,7 +287,7 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
                    int fixed_its, int *iters, double *resid, int *breakdown)
 {
     const int64_t n = c->ndof;
-    const int pr = c->prec;
+    const int pr = c->vprec;
     const size_t vb = c->rsz * (size_t)n;
     const int nb = reduce_blocks(n);
     void *v = c->kv[0], *R1 = c->kv[1], *R2 = c->kv[2], *Z = c->kv[3];
@@ -382,8 +386,9 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
         return fail(TMOP_ERR_ARG, "unknown target");
     if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
         return fail(TMOP_ERR_ARG, "target_h0 must be > 0");
-    if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32)
-        return fail(TMOP_ERR_ARG, "hess_precision must be TMOP_FP64 or TMOP_FP32");
+    if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32 &&
+        D.hess_precision != TMOP_FP64_NATIVE)
+        return fail(TMOP_ERR_ARG, "hess_precision must be TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE");
     if (D.num_elems > 0 && !elem_to_node) return fail(TMOP_ERR_ARG, "elem_to_node is NULL");
     const int64_t ndof = (int64_t)D.dim * D.num_nodes;
     int np = 1;
@@ -401,6 +406,8 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     for (int k = 0; k < D.dim; ++k) c->nqd *= D.nq1d;
     c->ns = (c->d * c->d) * (c->d * c->d + 1) / 2;
     c->prec = D.hess_precision;
+    c->vprec = c->prec == TMOP_FP32 ? TMOP_FP32 : TMOP_FP64;
+    c->arith = c->prec == TMOP_FP64_NATIVE ? ARITH_NATIVE : ARITH_DW;
     c->rsz = c->prec == TMOP_FP32 ? 4 : 8;
     c->E = D.num_elems;
     c->Nx = D.num_nodes;
@@ -463,17 +470,23 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     const int tabn = 2 * c->nq * c->ni + c->nq;
     std::vector<double> tab(tabn);
     std::vector<float> tabf(tabn);
+    std::vector<df> tabw(tabn);
     host_basis_tables(c->ni, c->nq, tab.data(), tab.data() + c->nq * c->ni,
                       tab.data() + 2 * c->nq * c->ni);
-    for (int i = 0; i < tabn; ++i) tabf[i] = (float)tab[i];
+    for (int i = 0; i < tabn; ++i) {
+        tabf[i] = (float)tab[i];
+        tabw[i] = df(tab[i]);
+    }
     STRY(c->alloc(&c->tab, tabn));
     STRY(c->alloc(&c->tabf, tabn));
+    STRY(c->alloc(&c->tabw, tabn));
+    SCK(cudaMemcpyAsync(c->tabw, tabw.data(), sizeof(df) * tabn, cudaMemcpyHostToDevice, c->stream));
     SCK(cudaMemcpyAsync(c->tab, tab.data(), sizeof(double) * tabn, cudaMemcpyHostToDevice, c->stream));
     SCK(cudaMemcpyAsync(c->tabf, tabf.data(), sizeof(float) * tabn, cudaMemcpyHostToDevice, c->stream));
     // stored Hessian data, element vectors, reductions, work vectors
     STRY(c->alloc_raw(&c->H, c->rsz * (size_t)c->E * c->ns * c->nqd));
     STRY(c->alloc(&c->ev64, (size_t)c->d * c->ENP));
-    if (c->prec == TMOP_FP32) STRY(c->alloc_raw(&c->evR, 4 * (size_t)c->d * c->ENP));
+    if (c->vprec == TMOP_FP32) STRY(c->alloc_raw(&c->evR, 4 * (size_t)c->d * c->ENP));
     else c->evR = c->ev64;
     const int64_t eb = elem_blocks(c->d, c->p, c->nq, c->E);
     c->part_n = std::max<int64_t>(2 * eb, 2 * 1184);
@@ -522,15 +535,15 @@ tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y)
     if (!ctx || !v || !y) return fail(TMOP_ERR_ARG, "NULL argument");
     if (v == y) return fail(TMOP_ERR_ARG, "v and y must not alias");
     if (!ctx->h_ready) return fail(TMOP_ERR_ARG, "tmop_hessian_setup has not been called");
-    CK(launch_mask(v, ctx->fixed, ctx->ndof, ctx->vm, ctx->prec, ctx->stream));
+    CK(launch_mask(v, ctx->fixed, ctx->ndof, ctx->vm, ctx->vprec, ctx->stream));
     const ElemParams P = ctx->params();
     TRY(timed(ctx, TMOP_K_APPLY, "apply kernel", [&] {
         return launch_apply(ctx->d, ctx->p, ctx->nq, P, ctx->vm, ctx->H, ctx->evR, ctx->prec,
                             nullptr, 0, ctx->stream);
     }));
     TRY(timed(ctx, TMOP_K_ASSEMBLE, "assemble", [&] {
-        return launch_assemble(ctx->evR, ctx->prec, ctx->csr_ptr, ctx->csr_idx, ctx->fixed, v, 1,
-                               ctx->Nx, ctx->d, ctx->ENP, y, ctx->prec, nullptr, 0, ctx->stream);
+        return launch_assemble(ctx->evR, ctx->vprec, ctx->csr_ptr, ctx->csr_idx, ctx->fixed, v, 1,
+                               ctx->Nx, ctx->d, ctx->ENP, y, ctx->vprec, nullptr, 0, ctx->stream);
     }));
     return TMOP_OK;
 }
@@ -575,7 +588,7 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
     if ((st = hsetup_async(c, x)) != TMOP_OK) return finish(st);
     if ((st = diag_async(c, c->diagR)) != TMOP_OK) return finish(st);
     {
-        cudaError_t e = launch_jacobi(c->diagR, c->prec, c->ndof, c->minv, c->stream);
+        cudaError_t e = launch_jacobi(c->diagR, c->vprec, c->ndof, c->minv, c->stream);
         if (e != cudaSuccess) return finish(cuda_fail(e, "jacobi"));
     }
     int its = 0, brk = 0;

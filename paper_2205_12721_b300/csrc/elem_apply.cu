@@ -3,16 +3,16 @@
 
 namespace tmop {
 
-template <class C, class R>
-static cudaError_t run_apply(const ElemParams &P, const R *v, const R *H, R *ev, const int *stop,
+template <class C, class RV, class RC>
+static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                              int k, cudaStream_t s)
 {
-    using L = Layout<C, R>;
+    using L = Layout<C, RC>;
     const int64_t nb = grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_apply<C, R>, L::bytes);
+    cudaError_t e = prepare(k_apply<C, RV, RC>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_apply<C, R><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+    k_apply<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
     count_launch();
     return cudaGetLastError();
 }
@@ -22,10 +22,14 @@ static cudaError_t run_apply_any(const ElemParams &P, const void *v, const void 
                                  int prec, const int *stop, int k, cudaStream_t s)
 {
     if (prec == TMOP_FP32)
-        return run_apply<C, float>(P, static_cast<const float *>(v), static_cast<const float *>(H),
-                                   static_cast<float *>(ev), stop, k, s);
-    return run_apply<C, double>(P, static_cast<const double *>(v), static_cast<const double *>(H),
-                                static_cast<double *>(ev), stop, k, s);
+        return run_apply<C, float, float>(P, static_cast<const float *>(v), static_cast<const float *>(H),
+                                          static_cast<float *>(ev), stop, k, s);
+    if (prec == TMOP_FP64_NATIVE)
+        return run_apply<C, double, double>(P, static_cast<const double *>(v),
+                                            static_cast<const double *>(H), static_cast<double *>(ev),
+                                            stop, k, s);
+    return run_apply<C, double, df>(P, static_cast<const double *>(v), static_cast<const df *>(H),
+                                    static_cast<double *>(ev), stop, k, s);
 }
 
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,

@@ -3,15 +3,15 @@
 
 namespace tmop {
 
-template <class C, class R>
-static cudaError_t run_diag(const ElemParams &P, const R *H, R *ev, cudaStream_t s)
+template <class C, class RV, class RC>
+static cudaError_t run_diag(const ElemParams &P, const RC *H, RV *ev, cudaStream_t s)
 {
-    using L = Layout<C, R>;
+    using L = Layout<C, RC>;
     const int64_t nb = grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_diag<C, R>, L::bytes);
+    cudaError_t e = prepare(k_diag<C, RV, RC>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_diag<C, R><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, H, ev);
+    k_diag<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, H, ev);
     count_launch();
     return cudaGetLastError();
 }
@@ -21,8 +21,10 @@ static cudaError_t run_diag_any(const ElemParams &P, const void *H, void *ev, in
                                 cudaStream_t s)
 {
     if (prec == TMOP_FP32)
-        return run_diag<C, float>(P, static_cast<const float *>(H), static_cast<float *>(ev), s);
-    return run_diag<C, double>(P, static_cast<const double *>(H), static_cast<double *>(ev), s);
+        return run_diag<C, float, float>(P, static_cast<const float *>(H), static_cast<float *>(ev), s);
+    if (prec == TMOP_FP64_NATIVE)
+        return run_diag<C, double, double>(P, static_cast<const double *>(H), static_cast<double *>(ev), s);
+    return run_diag<C, double, df>(P, static_cast<const df *>(H), static_cast<double *>(ev), s);
 }
 
 cudaError_t launch_diag(int d, int p, int q, const ElemParams &P, const void *H, void *ev, int prec,

@@ -1,49 +1,66 @@
 // Energy and gradient kernels: instantiation and launch for every supported
-// (dim, order, nq1d).
+// (dim, order, nq1d) and both contraction arithmetics (FP64 units or
+// double-float on the FP32 units).
 #include "elem_launch.cuh"
 
 namespace tmop {
 
-template <class C>
+template <class C, class RS>
 static cudaError_t run_energy(const ElemParams &P, const double *x, double *part, cudaStream_t s)
 {
-    using L = Layout<C, double>;
+    using L = Layout<C, RS>;
     const int64_t nb = grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_energy<C>, L::bytes);
+    cudaError_t e = prepare(k_energy<C, RS>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_energy<C><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, part);
+    k_energy<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class C, class RS>
+static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, cudaStream_t s)
+{
+    using L = Layout<C, RS>;
+    const int64_t nb = grid_of<C>(P.E);
+    if (nb == 0) return cudaSuccess;
+    cudaError_t e = prepare(k_gradient<C, RS>, L::bytes);
+    if (e != cudaSuccess) return e;
+    k_gradient<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev);
     count_launch();
     return cudaGetLastError();
 }
 
 template <class C>
-static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, cudaStream_t s)
+static cudaError_t run_energy_any(const ElemParams &P, const double *x, double *part, int arith,
+                                  cudaStream_t s)
 {
-    using L = Layout<C, double>;
-    const int64_t nb = grid_of<C>(P.E);
-    if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_gradient<C>, L::bytes);
-    if (e != cudaSuccess) return e;
-    k_gradient<C><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev);
-    count_launch();
-    return cudaGetLastError();
+    if (arith == ARITH_NATIVE) return run_energy<C, double>(P, x, part, s);
+    return run_energy<C, df>(P, x, part, s);
+}
+
+template <class C>
+static cudaError_t run_gradient_any(const ElemParams &P, const double *x, double *ev, int arith,
+                                    cudaStream_t s)
+{
+    if (arith == ARITH_NATIVE) return run_gradient<C, double>(P, x, ev, s);
+    return run_gradient<C, df>(P, x, ev, s);
 }
 
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
-                          cudaStream_t s)
+                          int arith, cudaStream_t s)
 {
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_energy<Cfg<D_, P_, Q_>>(P, x, part, s);
+    case TMOP_KEY(D_, P_, Q_): return run_energy_any<Cfg<D_, P_, Q_>>(P, x, part, arith, s);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }
 
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
-                            cudaStream_t s)
+                            int arith, cudaStream_t s)
 {
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_gradient<Cfg<D_, P_, Q_>>(P, x, ev, s);
+    case TMOP_KEY(D_, P_, Q_): return run_gradient_any<Cfg<D_, P_, Q_>>(P, x, ev, arith, s);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }

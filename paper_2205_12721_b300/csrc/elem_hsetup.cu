@@ -1,17 +1,18 @@
-// Partial-assembly setup kernels (stored d2mu/dT2 data, FP64 or FP32).
+// Partial-assembly setup kernels: stored d2mu/dT2 data in FP64 (native),
+// double-float pairs, or FP32.
 #include "elem_launch.cuh"
 
 namespace tmop {
 
-template <class C, class RH>
+template <class C, class RS, class RH>
 static cudaError_t run_hsetup(const ElemParams &P, const double *x, RH *H, cudaStream_t s)
 {
-    using L = Layout<C, double>;
+    using L = Layout<C, RS>;
     const int64_t nb = grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_hsetup<C, RH>, L::bytes);
+    cudaError_t e = prepare(k_hsetup<C, RS, RH>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_hsetup<C, RH><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, H);
+    k_hsetup<C, RS, RH><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, H);
     count_launch();
     return cudaGetLastError();
 }
@@ -20,8 +21,9 @@ template <class C>
 static cudaError_t run_hsetup_any(const ElemParams &P, const double *x, void *H, int prec,
                                   cudaStream_t s)
 {
-    if (prec == TMOP_FP32) return run_hsetup<C, float>(P, x, static_cast<float *>(H), s);
-    return run_hsetup<C, double>(P, x, static_cast<double *>(H), s);
+    if (prec == TMOP_FP32) return run_hsetup<C, df, float>(P, x, static_cast<float *>(H), s);
+    if (prec == TMOP_FP64_NATIVE) return run_hsetup<C, double, double>(P, x, static_cast<double *>(H), s);
+    return run_hsetup<C, df, df>(P, x, static_cast<df *>(H), s);
 }
 
 cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double *x, void *H,

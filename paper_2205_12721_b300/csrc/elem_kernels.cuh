@@ -30,11 +30,11 @@ struct ElemCtx {
 
 // Stage the tables and the element map; set up the thread's element slot.
 template <class C, class R>
-__device__ __forceinline__ void prologue(const ElemParams &P, const R *__restrict__ tab,
-                                         unsigned char *smem, ElemCtx<C, R> &c)
+__device__ __forceinline__ void prologue(const ElemParams &P, unsigned char *smem, ElemCtx<C, R> &c)
 {
     using L = Layout<C, R>;
     R *base = reinterpret_cast<R *>(smem);
+    const R *__restrict__ tab = table_of<R>(P);
     for (int i = threadIdx.x; i < L::TAB; i += C::NT) base[i] = tab[i];
     c.B = base;
     c.G = base + C::NQ * C::NI;
@@ -67,7 +67,7 @@ __device__ __forceinline__ void forward_component(const ElemParams &P, ElemCtx<C
                                                   const RIN *__restrict__ u, int a, bool want_x)
 {
     if (c.valid)
-        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = (R)u[a * P.Nx + c.smap[i]];
+        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = R(u[a * P.Nx + c.smap[i]]);
     __syncthreads();
     R *A0 = c.sA + (a * C::D) * C::NQD;
     R *xv = want_x ? c.sX + a * C::NQD : nullptr;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void backward_component(const ElemParams &P, ElemCtx<
         bwd2<C, R>(c.B, c.G, Y0, Y0 + C::NQD, c.s1, c.su, c.tx, c.ty, c.valid);
     if (c.valid)
         for (int i = c.t; i < C::NP; i += C::TPE)
-            ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = (ROUT)c.su[i];
+            ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = ROUT(to_d(c.su[i]));
 }
 
 // Iterate over this thread's quadrature points: (q1, q2) = (tx, ty), all q3.
@@ -108,45 +108,45 @@ __device__ __forceinline__ void for_my_points(int tx, int ty, bool valid, F &&f)
     }
 }
 
-template <class C>
-__device__ __forceinline__ double point_weight(const double *w, int tx, int ty, int q3)
+template <class C, class R>
+__device__ __forceinline__ double point_weight(const R *w, int tx, int ty, int q3)
 {
-    return C::D == 3 ? w[tx] * w[ty] * w[q3] : w[tx] * w[ty];
+    return C::D == 3 ? to_d(w[tx]) * to_d(w[ty]) * to_d(w[q3]) : to_d(w[tx]) * to_d(w[ty]);
 }
 
-template <class C>
-__device__ __forceinline__ double point_target(const ElemParams &P, const double *sX, int q)
+template <class C, class R>
+__device__ __forceinline__ double point_target(const ElemParams &P, const R *sX, int q)
 {
     double xq[3] = {0, 0, 0};
     if (P.target == TGT_SIZE)
 #pragma unroll
-        for (int k = 0; k < C::D; ++k) xq[k] = sX[k * C::NQD + q];
+        for (int k = 0; k < C::D; ++k) xq[k] = to_d(sX[k * C::NQD + q]);
     return target_scale<C::D>(P.target, P.h0, xq);
 }
 
 // ---------------------------------------------------------------- energy
-template <class C>
+// RS: arithmetic of the contractions (double, or df = double-float).
+template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
 k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, double> c;
-    prologue<C, double>(P, P.tab, smem, c);
+    ElemCtx<C, RS> c;
+    prologue<C, RS>(P, smem, c);
     const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
     double esum = 0.0, emin = INFINITY;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        double A[C::DD], T[C::DD], Cf[C::DD];
-#pragma unroll
-        for (int r = 0; r < C::DD; ++r) A[r] = c.sA[r * C::NQD + q];
+        double T[C::DD], Cf[C::DD];
         const double ws = point_target<C>(P, c.sX, q);
+        const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = A[r] / ws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
         const double detA = tau * wd;
@@ -176,168 +176,168 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part)
 }
 
 // ---------------------------------------------------------------- gradient
-template <class C>
+template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
 k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, double> c;
-    prologue<C, double>(P, P.tab, smem, c);
+    ElemCtx<C, RS> c;
+    prologue<C, RS>(P, smem, c);
     const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
         const double ws = point_target<C>(P, c.sX, q);
+        const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = c.sA[r * C::NQD + q] / ws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
         if (!(tau > 0.0)) {                               // inverted points contribute 0
 #pragma unroll
-            for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = 0.0;
+            for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0);
             return;
         }
         Inv v;
         metric_scalars(P.metric, I1, tau, I2, v);
         if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
-        const double sc = cq / ws;
+        const double sc = cq * iws;
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) {
             double pr = v.f1 * 2.0 * T[r] + v.ft * Cf[r];
             if (C::D == 3 && v.f2 != 0.0) pr += v.f2 * g2[r];
-            c.sA[r * C::NQD + q] = sc * pr;
+            c.sA[r * C::NQD + q] = RS(sc * pr);
         }
     });
     __syncthreads();
-    for (int a = 0; a < C::D; ++a) backward_component<C, double, double>(P, c, ev, a);
+    for (int a = 0; a < C::D; ++a) backward_component<C, RS, double>(P, c, ev, a);
 }
 
 // ---------------------------------------------------------------- Hessian setup
-template <class C, class RH>
+template <class C, class RS, class RH>
 __global__ void __launch_bounds__(C::NT)
 k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, double> c;
-    prologue<C, double>(P, P.tab, smem, c);
+    ElemCtx<C, RS> c;
+    prologue<C, RS>(P, smem, c);
     const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, double, double>(P, c, x, a, want_x);
+    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
     RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
         const double ws = point_target<C>(P, c.sX, q);
+        const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = c.sA[r * C::NQD + q] / ws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
         if (!(tau > 0.0)) {                               // inverted points store 0
 #pragma unroll
-            for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = (RH)0;
+            for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0);
             return;
         }
         Inv v;
         metric_scalars(P.metric, I1, tau, I2, v);
         if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
-        const double sc = cq / (ws * ws);
+        const double sc = cq * iws * iws;
 #pragma unroll
         for (int r = 0; r < C::DD; ++r)
 #pragma unroll
             for (int s = r; s < C::DD; ++s)
                 He[pidx<C::DD>(r, s) * C::NQD + q] =
-                    (RH)(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+                    RH(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
     });
 }
 
 // ---------------------------------------------------------------- Hessian action
-// v is expected to be zero on fixed DOFs (callers mask it first).
-// If stop_iter != nullptr and *stop_iter < k the launch does nothing (MINRES
-// iterations after convergence).
-template <class C, class R>
+// RV: type of v and of the element vector; RC: arithmetic and stored data
+// (double, float, or df with double vectors).  v is expected to be zero on
+// fixed DOFs (callers mask it first).  If stop_iter != nullptr and
+// *stop_iter < k the launch does nothing (MINRES iterations after
+// convergence).
+template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
-k_apply(ElemParams P, const R *__restrict__ v, const R *__restrict__ H, R *__restrict__ ev,
+k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
         const int *__restrict__ stop_iter, int k)
 {
     if (stop_iter && *stop_iter < k) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, R> c;
-    const R *tab = sizeof(R) == 8 ? reinterpret_cast<const R *>(P.tab)
-                                  : reinterpret_cast<const R *>(P.tabf);
-    prologue<C, R>(P, tab, smem, c);
-    for (int a = 0; a < C::D; ++a) forward_component<C, R, R>(P, c, v, a, false);
+    ElemCtx<C, RC> c;
+    prologue<C, RC>(P, smem, c);
+    for (int a = 0; a < C::D; ++a) forward_component<C, RC, RV>(P, c, v, a, false);
 
-    const R *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
-        R dA[C::DD], h[C::NS];
+        RC dA[C::DD], h[C::NS];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) dA[r] = c.sA[r * C::NQD + q];
 #pragma unroll
         for (int s = 0; s < C::NS; ++s) h[s] = He[s * C::NQD + q];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) {
-            R y = 0;
+            RC y = 0;
 #pragma unroll
             for (int s = 0; s < C::DD; ++s) y += h[r <= s ? pidx<C::DD>(r, s) : pidx<C::DD>(s, r)] * dA[s];
             c.sA[r * C::NQD + q] = y;
         }
     });
     __syncthreads();
-    for (int a = 0; a < C::D; ++a) backward_component<C, R, R>(P, c, ev, a);
+    for (int a = 0; a < C::D; ++a) backward_component<C, RC, RV>(P, c, ev, a);
 }
 
 // ---------------------------------------------------------------- diagonal
 // diag_{a,i} = sum_q sum_{b,e} H_{ab,ae}(q) d_b w_i(q) d_e w_i(q); the
 // product d_b w_i d_e w_i factors per direction k into (B or G)(B or G).
-template <class C, class R>
+template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
-k_diag(ElemParams P, const R *__restrict__ H, R *__restrict__ ev)
+k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, R> c;
-    const R *tab = sizeof(R) == 8 ? reinterpret_cast<const R *>(P.tab)
-                                  : reinterpret_cast<const R *>(P.tabf);
-    prologue<C, R>(P, tab, smem, c);
-    __shared__ R tbl[3][C::NQ * C::NI];          // B*B, B*G, G*G (elementwise)
+    ElemCtx<C, RC> c;
+    prologue<C, RC>(P, smem, c);
+    __shared__ RC tbl[3][C::NQ * C::NI];          // B*B, B*G, G*G (elementwise)
     for (int i = threadIdx.x; i < C::NQ * C::NI; i += C::NT) {
-        tbl[0][i] = c.B[i] * c.B[i];
-        tbl[1][i] = c.B[i] * c.G[i];
-        tbl[2][i] = c.G[i] * c.G[i];
+        tbl[0][i] = prod(c.B[i], c.B[i]);
+        tbl[1][i] = prod(c.B[i], c.G[i]);
+        tbl[2][i] = prod(c.G[i], c.G[i]);
     }
     __syncthreads();
-    const R *He = H + c.e * (int64_t)(C::NS * C::NQD);
-    R *f = c.sA;
+    const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    RC *f = c.sA;
     for (int a = 0; a < C::D; ++a) {
         if (c.valid)
-            for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = 0;
+            for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = RC(0.0);
         for (int b = 0; b < C::D; ++b)
             for (int e2 = b; e2 < C::D; ++e2) {
                 const int r = a * C::D + b, s = a * C::D + e2;
-                const R scale = (b == e2) ? R(1) : R(2);
+                const RC scale = (b == e2) ? RC(1.0) : RC(2.0);
                 for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
-                    f[q] = scale * He[pidx<C::DD>(r, s) * C::NQD + q];
+                    f[q] = prod(scale, He[pidx<C::DD>(r, s) * C::NQD + q]);
                 });
                 __syncthreads();
-                const R *T1 = tbl[(b == 0) + (e2 == 0)];
-                const R *T2 = tbl[(b == 1) + (e2 == 1)];
+                const RC *T1 = tbl[(b == 0) + (e2 == 0)];
+                const RC *T2 = tbl[(b == 1) + (e2 == 1)];
                 if (C::D == 3) {
-                    const R *T3 = tbl[(b == 2) + (e2 == 2)];
-                    bwd3_tab<C, R>(T1, T2, T3, f, c.s1, c.s2, c.su, c.tx, c.ty, c.valid);
+                    const RC *T3 = tbl[(b == 2) + (e2 == 2)];
+                    bwd3_tab<C, RC>(T1, T2, T3, f, c.s1, c.s2, c.su, c.tx, c.ty, c.valid);
                 } else {
-                    bwd2_tab<C, R>(T1, T2, f, c.s1, c.su, c.tx, c.ty, c.valid);
+                    bwd2_tab<C, RC>(T1, T2, f, c.s1, c.su, c.tx, c.ty, c.valid);
                 }
             }
         if (c.valid)
             for (int i = c.t; i < C::NP; i += C::TPE)
-                ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = c.su[i];
+                ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = RV(to_d(c.su[i]));
         __syncthreads();
     }
 }

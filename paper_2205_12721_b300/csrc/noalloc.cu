@@ -15,7 +15,8 @@ namespace {
 constexpr int kMaxCtas = 65536;                   // partial (sum, min) pairs
 constexpr int kTableOffset = 2 * kMaxCtas;        // 1D tables follow the partials
 constexpr int kTableMax = 128;                    // >= 2 nq (p+1) + nq for p <= 4, nq <= 6
-constexpr int kScratchDoubles = kTableOffset + kTableMax;
+// FP64 tables, then the same tables as double-float pairs (8 bytes each)
+constexpr int kScratchDoubles = kTableOffset + 2 * kTableMax;
 
 // Shared by every call in the process on this device; holds the last call's
 // contents until the library is unloaded.
@@ -86,10 +87,12 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
 
     // 1D tables on the host stack, copied into the scratch array
     const int ni = D.order + 1, nq = D.nq1d;
-    double tab[kTableMax];
+    double tab[2 * kTableMax];
     host_basis_tables(ni, nq, tab, tab + nq * ni, tab + 2 * nq * ni);
     const int tabn = 2 * nq * ni + nq;
-    cudaError_t e = cudaMemcpyAsync(scratch + kTableOffset, tab, sizeof(double) * tabn,
+    df *tabw = reinterpret_cast<df *>(tab + kTableMax);
+    for (int i = 0; i < tabn; ++i) tabw[i] = df(tab[i]);
+    cudaError_t e = cudaMemcpyAsync(scratch + kTableOffset, tab, sizeof(double) * 2 * kTableMax,
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("table copy: ") + cudaGetErrorString(e));
 
@@ -99,12 +102,14 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
     P.Nx = D.num_nodes;
     P.tab = scratch + kTableOffset;
     P.tabf = nullptr;
+    P.tabw = reinterpret_cast<const df *>(scratch + kTableOffset + kTableMax);
     P.metric = D.metric;
     P.target = D.target;
     P.h0 = D.target_h0;
     // every partial slot the reduction reads is written by this launch, so
     // nothing in the scratch needs clearing first
-    e = launch_energy(D.dim, D.order, D.nq1d, P, x, scratch, s);
+    const int arith = D.hess_precision == TMOP_FP64_NATIVE ? ARITH_NATIVE : ARITH_DW;
+    e = launch_energy(D.dim, D.order, D.nq1d, P, x, scratch, arith, s);
     if (e == cudaSuccess) e = launch_finalize_energy(scratch, nb, out, s);
     if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("energy launch: ") + cudaGetErrorString(e));
     return TMOP_OK;

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace tmop {
 
 enum { MET_2 = 2, MET_55 = 55, MET_302 = 302, MET_303 = 303, MET_303_55 = 30355 };
@@ -43,6 +45,7 @@ struct ElemParams {
     int64_t E, Nx;
     const double *__restrict__ tab;    // B[NQ*NI], G[NQ*NI], w1d[NQ]
     const float *__restrict__ tabf;    // same, FP32
+    const df *__restrict__ tabw;       // same, double-float
     int metric, target;
     double h0;
 };
@@ -497,6 +500,17 @@ __device__ __forceinline__ double target_scale(int target, double h0, const doub
     s += 1.0;
     return h0 * (D == 3 ? cbrt(s) : sqrt(s));
 }
+
+// Table of the compute type R.
+template <class R> __device__ __forceinline__ const R *table_of(const ElemParams &P);
+template <> __device__ __forceinline__ const double *table_of<double>(const ElemParams &P) { return P.tab; }
+template <> __device__ __forceinline__ const float *table_of<float>(const ElemParams &P) { return P.tabf; }
+template <> __device__ __forceinline__ const df *table_of<df>(const ElemParams &P) { return P.tabw; }
+
+// Normalised product in the compute type.
+__device__ __forceinline__ double prod(double a, double b) { return a * b; }
+__device__ __forceinline__ float prod(float a, float b) { return a * b; }
+__device__ __forceinline__ df prod(const df &a, const df &b) { return to_df(a * b); }
 
 // Packed index of (r, s), r <= s, in a row-major upper triangle of size DD.
 template <int DD>

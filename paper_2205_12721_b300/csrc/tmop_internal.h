@@ -19,14 +19,17 @@ namespace tmop {
 
 struct ElemParams;
 
+// Arithmetic of the FP64-accuracy contractions (energy, gradient, setup).
+enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
+
 // Element-kernel launchers (one translation unit each).  Return the launch
 // error.  nblocks() is the grid size a launch over E elements uses.
 int64_t elem_blocks(int d, int p, int q, int64_t E);
 bool elem_supported(int d, int p, int q);
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
-                          cudaStream_t s);
+                          int arith, cudaStream_t s);
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
-                            cudaStream_t s);
+                            int arith, cudaStream_t s);
 cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double *x, void *H,
                           int prec, cudaStream_t s);
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,

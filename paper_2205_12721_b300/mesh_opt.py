@@ -13,7 +13,8 @@ class TmopMesh:
     ``map`` (E x (p+1)^d int32), ``fixed`` (d*Nx uint8 or None) are copied to
     the device once.  Positions and vectors are torch CUDA tensors of length
     d*Nx in component-major order (float64; float32 for the Hessian action
-    of a ``precision="fp32"`` context).
+    of a ``precision="fp32"`` context).  ``precision``: "fp64" (double-float
+    contractions on the FP32 units), "fp32" (mixed) or "fp64-native".
     """
 
     def __init__(self, dim, order, emap, num_nodes, metric, fixed=None, nq1d=None,
@@ -24,7 +25,7 @@ class TmopMesh:
         self.num_nodes = int(num_nodes)
         self.ndof = dim * self.num_nodes
         self.device = torch.device(device)
-        self.prec = capi.FP32 if precision == "fp32" else capi.FP64
+        self.prec = {"fp64": capi.FP64, "fp32": capi.FP32, "fp64-native": capi.FP64_NATIVE}[precision]
         self.rdtype = torch.float32 if self.prec == capi.FP32 else torch.float64
         emap = np.ascontiguousarray(emap, dtype=np.int32)
         self.num_elems = int(emap.shape[0])

@@ -31,14 +31,21 @@ def _ids(c):
     return f"d{c[0]}p{c[1]}q{c[2]}m{c[3]}t{c[4]}"
 
 
-@pytest.mark.parametrize("case", CASES, ids=_ids)
-def test_fp64_parity(case):
+NATIVE_CASES = [(2, 2, 3, 2, 0), (2, 4, 6, 2, 0), (3, 1, 2, 302, 0), (3, 3, 4, 303, 0),
+                (3, 4, 5, 302, 0), (3, 2, 3, 30355, 1)]
+PARAMS = [(c, "fp64") for c in CASES] + [(c, "fp64-native") for c in NATIVE_CASES]
+
+
+@pytest.mark.parametrize("case,precision", PARAMS, ids=[f"{_ids(c)}-{p}" for c, p in PARAMS])
+def test_fp64_parity(case, precision):
+    """FP64-class contexts: double-float contractions (default) and the
+    native FP64-unit path."""
     d, p, nq, metric, target = case
     for si, shape in enumerate(SHAPES[d]):
         m = make_case(d, p, shape, seed=10 + si)
         h0 = 1.0 / max(shape)
         om = oracle_mesh(m, metric, nq, target, h0)
-        gm = gpu_mesh(m, metric, nq, target, h0)
+        gm = gpu_mesh(m, metric, nq, target, h0, precision=precision)
         x = dev(m.x)
         # energy and min det
         st_o, F_o, md_o, S = O.energy(om, m.x)
