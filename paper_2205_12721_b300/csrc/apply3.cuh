@@ -1,0 +1,214 @@
+// 3D Hessian action with thread-local quadrature columns (sm_103a).
+//
+// y = G^T B^T (H : B G v) (paper Sec. 3.4, eq. vm_pa_hess) for one element
+// per MX x MX thread square.  A thread owning (q1, q2) keeps the nine
+// reference-gradient components dA_{cb}(q1, q2, q3) of its q3 column in
+// registers from the last forward contraction, through the pointwise product
+// with the stored data, into the first transposed contraction, so no
+// per-point array lives in shared memory: an element needs only the node
+// block and the two intermediate tensors (384 values for p = 3), which keeps
+// more elements resident per SM than the generic kernel.  Accumulations use
+// the unnormalised acc_add (normalised once per stored value).
+#pragma once
+
+#include "elem_kernels.cuh"
+
+namespace tmop {
+
+template <class C, class R>
+struct Apply3Layout {
+    static constexpr int TAB = 2 * C::NQ * C::NI;                       // B, G
+    static constexpr int TAB_PAD = (TAB + 1) & ~1;
+    static constexpr int SLOT = (C::SU + C::S1 + C::S2 + 1) & ~1;
+    static constexpr size_t bytes = sizeof(R) * (size_t)(TAB_PAD + C::EPB * SLOT) +
+                                    sizeof(int) * (size_t)(C::EPB * C::NP);
+};
+
+template <class C, class RV, class RC>
+__global__ void __launch_bounds__(C::NT)
+k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
+         const int *__restrict__ stop_iter, int k)
+{
+    static_assert(C::D == 3, "3D kernel");
+    constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP, NQD = C::NQD, NS = C::NS;
+    constexpr int O1 = NI * NI * NQ, O2 = NI * NQ * NQ;
+    using L = Apply3Layout<C, RC>;
+    if (stop_iter && *stop_iter < k) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    RC *base = reinterpret_cast<RC *>(smem);
+    const RC *__restrict__ tab = table_of<RC>(P);
+    for (int i = threadIdx.x; i < L::TAB; i += C::NT) base[i] = tab[i];
+    const RC *B = base, *G = base + NQ * NI;
+    const int slot = threadIdx.x / C::TPE;
+    const bool act = slot < C::EPB;
+    const int sl = act ? slot : 0;
+    const int t = threadIdx.x - slot * C::TPE;
+    const int tx = t % C::MX, ty = t / C::MX;
+    RC *su = base + L::TAB_PAD + sl * L::SLOT;
+    RC *s1 = su + C::SU;
+    RC *s2 = s1 + C::S1;
+    int *smap = reinterpret_cast<int *>(base + L::TAB_PAD + C::EPB * L::SLOT) + sl * NP;
+    const int64_t e = (int64_t)blockIdx.x * C::EPB + sl;
+    const bool valid = act && e < P.E;
+    if (valid)
+        for (int i = t; i < NP; i += C::TPE) smap[i] = P.map[e * NP + i];
+    __syncthreads();
+
+    const bool qq = valid && tx < NQ && ty < NQ;     // owns a quadrature column
+    RC col[9][NQ];                                   // dA_{cb} then Y_{cb} at (tx, ty, q3)
+
+    // ---- forward: three contractions per component, the last into registers
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        if (valid)
+            for (int i = t; i < NP; i += C::TPE) su[i] = RC(v[c * P.Nx + smap[i]]);
+        __syncthreads();
+        if (valid && tx < NQ && ty < NI) {
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                RC b = 0, g = 0;
+#pragma unroll
+                for (int i1 = 0; i1 < NI; ++i1) {
+                    const RC u = su[(i3 * NI + ty) * NI + i1];
+                    acc_add(b, B[tx * NI + i1] * u);
+                    acc_add(g, G[tx * NI + i1] * u);
+                }
+                s1[(i3 * NI + ty) * NQ + tx] = norm(b);
+                s1[O1 + (i3 * NI + ty) * NQ + tx] = norm(g);
+            }
+        }
+        __syncthreads();
+        if (qq) {
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                RC bb = 0, bg = 0, gb = 0;
+#pragma unroll
+                for (int i2 = 0; i2 < NI; ++i2) {
+                    const RC sb = s1[(i3 * NI + i2) * NQ + tx];
+                    const RC sg = s1[O1 + (i3 * NI + i2) * NQ + tx];
+                    const RC Bq = B[ty * NI + i2], Gq = G[ty * NI + i2];
+                    acc_add(bb, Bq * sb);
+                    acc_add(bg, Gq * sb);
+                    acc_add(gb, Bq * sg);
+                }
+                s2[(i3 * NQ + ty) * NQ + tx] = norm(gb);
+                s2[O2 + (i3 * NQ + ty) * NQ + tx] = norm(bg);
+                s2[2 * O2 + (i3 * NQ + ty) * NQ + tx] = norm(bb);
+            }
+        }
+        __syncthreads();
+        if (qq) {
+            RC c0[NI], c1[NI], c2[NI];
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                c0[i3] = s2[(i3 * NQ + ty) * NQ + tx];
+                c1[i3] = s2[O2 + (i3 * NQ + ty) * NQ + tx];
+                c2[i3] = s2[2 * O2 + (i3 * NQ + ty) * NQ + tx];
+            }
+#pragma unroll
+            for (int q3 = 0; q3 < NQ; ++q3) {
+                RC r0 = 0, r1 = 0, r2 = 0;
+#pragma unroll
+                for (int i3 = 0; i3 < NI; ++i3) {
+                    const RC Bq = B[q3 * NI + i3], Gq = G[q3 * NI + i3];
+                    acc_add(r0, Bq * c0[i3]);
+                    acc_add(r1, Bq * c1[i3]);
+                    acc_add(r2, Gq * c2[i3]);
+                }
+                // component c is constant inside this unrolled body per c value
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    if (cc == c) {
+                        col[cc * 3 + 0][q3] = norm(r0);
+                        col[cc * 3 + 1][q3] = norm(r1);
+                        col[cc * 3 + 2][q3] = norm(r2);
+                    }
+            }
+        }
+    }
+
+    // ---- pointwise: Y = H : dA with the symmetric-packed stored data
+    if (qq) {
+        const RC *He = H + e * (int64_t)(NS * NQD) + (ty * NQ + tx);
+#pragma unroll
+        for (int q3 = 0; q3 < NQ; ++q3) {
+            RC y[9];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) y[r] = 0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r)
+#pragma unroll
+                for (int s = r; s < 9; ++s) {
+                    const RC h = He[pidx<9>(r, s) * NQD + q3 * NQ * NQ];
+                    acc_add(y[r], h * col[s][q3]);
+                    if (s != r) acc_add(y[s], h * col[r][q3]);
+                }
+#pragma unroll
+            for (int r = 0; r < 9; ++r) col[r][q3] = norm(y[r]);
+        }
+    }
+
+    // ---- transposed contractions per component, first one from registers
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        if (qq) {
+            RC y0[NQ], y1[NQ], y2[NQ];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+                if (cc == c) {
+#pragma unroll
+                    for (int q3 = 0; q3 < NQ; ++q3) {
+                        y0[q3] = col[cc * 3 + 0][q3];
+                        y1[q3] = col[cc * 3 + 1][q3];
+                        y2[q3] = col[cc * 3 + 2][q3];
+                    }
+                }
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                RC z0 = 0, z1 = 0, z2 = 0;
+#pragma unroll
+                for (int q3 = 0; q3 < NQ; ++q3) {
+                    const RC Bq = B[q3 * NI + i3], Gq = G[q3 * NI + i3];
+                    acc_add(z0, Bq * y0[q3]);
+                    acc_add(z1, Bq * y1[q3]);
+                    acc_add(z2, Gq * y2[q3]);
+                }
+                s2[(i3 * NQ + ty) * NQ + tx] = norm(z0);
+                s2[O2 + (i3 * NQ + ty) * NQ + tx] = norm(z1);
+                s2[2 * O2 + (i3 * NQ + ty) * NQ + tx] = norm(z2);
+            }
+        }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NI) {
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                RC a = 0, b = 0;
+#pragma unroll
+                for (int q2 = 0; q2 < NQ; ++q2) {
+                    const RC Bq = B[q2 * NI + ty], Gq = G[q2 * NI + ty];
+                    acc_add(a, Bq * s2[(i3 * NQ + q2) * NQ + tx]);
+                    acc_add(b, Gq * s2[O2 + (i3 * NQ + q2) * NQ + tx]);
+                    acc_add(b, Bq * s2[2 * O2 + (i3 * NQ + q2) * NQ + tx]);
+                }
+                s1[(i3 * NI + ty) * NQ + tx] = norm(a);
+                s1[O1 + (i3 * NI + ty) * NQ + tx] = norm(b);
+            }
+        }
+        __syncthreads();
+        if (valid && tx < NI && ty < NI) {
+            RV *out = ev + (int64_t)c * P.E * NP + e * NP;
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                RC o = 0;
+#pragma unroll
+                for (int q1 = 0; q1 < NQ; ++q1) {
+                    acc_add(o, G[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1]);
+                    acc_add(o, B[q1 * NI + tx] * s1[O1 + (i3 * NI + ty) * NQ + q1]);
+                }
+                out[(i3 * NI + ty) * NI + tx] = RV(to_d(norm(o)));
+            }
+        }
+    }
+}
+
+}  // namespace tmop

@@ -83,6 +83,25 @@ __device__ __forceinline__ df operator+(const df &a, const df &b)
     return add_norm(a.h, b.h, a.l + b.l);
 }
 
+// Unnormalised accumulation acc += a*b: exact TwoSum of the high parts, the
+// low parts and the rounding error summed in the low word without the final
+// renormalisation (|l| may grow to a few ulp(h) over a short sum; norm()
+// restores the invariant).  Used for the fixed-length contractions.
+__device__ __forceinline__ void acc_add(df &a, const dprod &b)
+{
+    const float s = a.h + b.p;
+    const float bb = s - a.h;
+    const float err = (a.h - (s - bb)) + (b.p - bb);
+    a.l = a.l + b.e + err;
+    a.h = s;
+}
+__device__ __forceinline__ void acc_add(double &a, double b) { a += b; }
+__device__ __forceinline__ void acc_add(float &a, float b) { a += b; }
+
+__device__ __forceinline__ df norm(const df &a) { return fast_two_sum(a.h, a.l); }
+__device__ __forceinline__ double norm(double a) { return a; }
+__device__ __forceinline__ float norm(float a) { return a; }
+
 // Normalised value of a product.
 __device__ __forceinline__ df to_df(const dprod &a) { return fast_two_sum(a.p, a.e); }
 __device__ __forceinline__ df to_df(const df &a) { return a; }

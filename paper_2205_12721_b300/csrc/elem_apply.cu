@@ -1,4 +1,5 @@
 // Hessian-action kernels (the dominant kernel of the Newton step).
+#include "apply3.cuh"
 #include "elem_launch.cuh"
 
 namespace tmop {
@@ -7,12 +8,19 @@ template <class C, class RV, class RC>
 static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                              int k, cudaStream_t s)
 {
-    using L = Layout<C, RC>;
     const int64_t nb = grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_apply<C, RV, RC>, L::bytes);
-    if (e != cudaSuccess) return e;
-    k_apply<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+    if constexpr (C::D == 3) {
+        using L = Apply3Layout<C, RC>;
+        cudaError_t e = prepare(k_apply3<C, RV, RC>, L::bytes);
+        if (e != cudaSuccess) return e;
+        k_apply3<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+    } else {
+        using L = Layout<C, RC>;
+        cudaError_t e = prepare(k_apply<C, RV, RC>, L::bytes);
+        if (e != cudaSuccess) return e;
+        k_apply<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -339,6 +339,13 @@ __device__ __forceinline__ void bwd2_tab(const R *__restrict__ T1, const R *__re
 //   dmu/dT       = f1 g1 + ft gt + f2 g2
 //   d2mu/dT2     = f1 2Id + ft d2tau + f2 d2I2 + sum_uv f_uv g_u (x) g_v.
 // -------------------------------------------------------------------------
+// Packed index of (r, s), r <= s, in a row-major upper triangle of size DD.
+template <int DD>
+__host__ __device__ constexpr int pidx(int r, int s)
+{
+    return r * DD - r * (r - 1) / 2 + (s - r);
+}
+
 struct Inv {
     double f1, ft, f2;               // first derivatives of mu w.r.t. (I1, tau, I2)
     double f11, f1t, ftt, f12, f2t;  // second derivatives (f22 = 0 for all metrics)
@@ -512,11 +519,5 @@ __device__ __forceinline__ double prod(double a, double b) { return a * b; }
 __device__ __forceinline__ float prod(float a, float b) { return a * b; }
 __device__ __forceinline__ df prod(const df &a, const df &b) { return to_df(a * b); }
 
-// Packed index of (r, s), r <= s, in a row-major upper triangle of size DD.
-template <int DD>
-__host__ __device__ constexpr int pidx(int r, int s)
-{
-    return r * DD - r * (r - 1) / 2 + (s - r);
-}
 
 }  // namespace tmop
