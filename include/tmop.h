@@ -214,6 +214,70 @@ tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *o
 tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t *elem_to_node,
                                 const double *x, double *out, void *cuda_stream);
 
+/* ---- Batches of meshes (many small problems in shared launches) --------
+ * A batch holds up to max_meshes independent meshes that share dim, order,
+ * nq1d, metric, target and precision but not their sizes.  Each mesh keeps
+ * its own resident state (positions, map, stored Hessian data, Krylov
+ * vectors) on the device; tmop_batch_step runs one Newton step (Sec. 2.3) of
+ * every active mesh with shared kernel launches over all of their elements
+ * and DOFs, with per-mesh scalars, per-mesh MINRES recurrences and per-mesh
+ * line searches.  A mesh stops when |dF(x)|/|dF(x0)| <= newton_rtol, after
+ * newton_max_it steps, or on an error (its status).  Meshes can be added and
+ * removed between steps (continuous batching).  A mesh's results do not
+ * depend on the other meshes of the batch (per-mesh reductions in a fixed
+ * order). */
+typedef struct {
+    int dim, order, nq1d, metric, target, hess_precision;
+    int max_meshes;              /* slot capacity */
+    tmop_solver_opts solver;     /* MINRES and line-search options */
+    double newton_rtol;          /* stop when |dF| <= newton_rtol |dF(x0)| */
+    int newton_max_it;           /* Newton step cap per mesh */
+} tmop_batch_desc;
+
+typedef struct {
+    int done;          /* 1 when the mesh needs no more steps */
+    int status;        /* tmop_status of the mesh (TMOP_OK if converged or capped) */
+    int newton_its;    /* accepted Newton steps */
+    int minres_its;    /* total MINRES iterations */
+    double energy0, energy, grad_norm0, grad_norm, min_det, alpha;
+} tmop_mesh_state;
+
+typedef struct tmop_batch tmop_batch;
+
+/* Create an empty batch working on the given stream.  Errors as tmop_setup. */
+tmop_status tmop_batch_create(const tmop_batch_desc *desc, void *cuda_stream, tmop_batch **out);
+
+/* Add a mesh: elem_to_node (device int32), fixed (device uint8 dim*num_nodes
+ * or NULL) and the initial positions x (device FP64) are copied into a new
+ * device slab owned by the batch; target_h0 is the mesh's size-target scale.
+ * slot (host) receives its handle.  Synchronises the stream.  Errors:
+ * TMOP_ERR_ARG (full batch, bad map), TMOP_ERR_OOM. */
+tmop_status tmop_batch_add(tmop_batch *b, int64_t num_elems, int64_t num_nodes,
+                           const int32_t *elem_to_node, const uint8_t *fixed, const double *x,
+                           double target_h0, int *slot);
+
+/* One Newton step of every active mesh.  n_active (host, may be NULL)
+ * receives the number of meshes still active afterwards.  Synchronises. */
+tmop_status tmop_batch_step(tmop_batch *b, int *n_active);
+
+/* State of one mesh after the last step (host struct). */
+tmop_status tmop_batch_state(tmop_batch *b, int slot, tmop_mesh_state *st);
+
+/* Copy a mesh's current positions to x_out (device FP64, dim*num_nodes);
+ * asynchronous on the batch stream. */
+tmop_status tmop_batch_positions(tmop_batch *b, int slot, double *x_out);
+
+/* Free a mesh's slab and its slot (between steps). */
+tmop_status tmop_batch_remove(tmop_batch *b, int slot);
+
+/* Device bytes a mesh of this size would take in this batch, and the bytes
+ * the batch holds now (for admission by a memory budget). */
+int64_t tmop_batch_mesh_bytes(const tmop_batch *b, int64_t num_elems, int64_t num_nodes);
+int64_t tmop_batch_device_bytes(const tmop_batch *b);
+
+/* Free the batch and all its meshes.  NULL is accepted. */
+void tmop_batch_destroy(tmop_batch *b);
+
 /* Free the context and everything it owns.  NULL is accepted. */
 void tmop_destroy(tmop_ctx *ctx);
 

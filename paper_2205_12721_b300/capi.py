@@ -25,7 +25,10 @@ K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)
 EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_hessian_apply", "tmop_hessian_diag", "tmop_newton_step", "tmop_destroy",
            "tmop_status_string", "tmop_last_error", "tmop_launch_count", "tmop_profile_enable",
-           "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc")
+           "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc",
+           "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
+           "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
+           "tmop_batch_device_bytes", "tmop_batch_destroy")
 
 
 class TmopError(RuntimeError):
@@ -53,6 +56,25 @@ class StepReport(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("min_det", ctypes.c_double),
                 ("minres_resid", ctypes.c_double), ("minres_iters", ctypes.c_int),
                 ("halvings", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("nq1d", ctypes.c_int),
+                ("metric", ctypes.c_int), ("target", ctypes.c_int),
+                ("hess_precision", ctypes.c_int), ("max_meshes", ctypes.c_int),
+                ("solver", SolverOpts), ("newton_rtol", ctypes.c_double),
+                ("newton_max_it", ctypes.c_int)]
+
+
+class MeshState(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("newton_its", ctypes.c_int),
+                ("minres_its", ctypes.c_int), ("energy0", ctypes.c_double),
+                ("energy", ctypes.c_double), ("grad_norm0", ctypes.c_double),
+                ("grad_norm", ctypes.c_double), ("min_det", ctypes.c_double),
+                ("alpha", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,6 +108,15 @@ def lib():
             "tmop_profile_read": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]),
             "tmop_device_bytes": (I64, [P]),
             "tmop_energy_noalloc": (I, [ctypes.POINTER(Desc), P, P, P, P]),
+            "tmop_batch_create": (I, [ctypes.POINTER(BatchDesc), P, ctypes.POINTER(P)]),
+            "tmop_batch_add": (I, [P, I64, I64, P, P, P, D, ctypes.POINTER(I)]),
+            "tmop_batch_step": (I, [P, ctypes.POINTER(I)]),
+            "tmop_batch_state": (I, [P, I, ctypes.POINTER(MeshState)]),
+            "tmop_batch_positions": (I, [P, I, P]),
+            "tmop_batch_remove": (I, [P, I]),
+            "tmop_batch_mesh_bytes": (I64, [P, I64, I64]),
+            "tmop_batch_device_bytes": (I64, [P]),
+            "tmop_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -197,3 +228,57 @@ def tmop_energy_noalloc(desc: Desc, elem_to_node, x, out, stream=None):
         stream = stream.cuda_stream
     return lib().tmop_energy_noalloc(ctypes.byref(desc), _ptr(elem_to_node), _ptr(x), _ptr(out),
                                      stream)
+
+
+# ---------------------------------------------------------------- batches
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def tmop_batch_create(desc: BatchDesc, stream=None) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().tmop_batch_create(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(out)),
+           "tmop_batch_create")
+    return out.value
+
+
+def tmop_batch_add(b: int, num_elems: int, num_nodes: int, elem_to_node, fixed, x, h0=1.0) -> int:
+    slot = ctypes.c_int()
+    _check(lib().tmop_batch_add(b, num_elems, num_nodes, _ptr(elem_to_node), _ptr(fixed), _ptr(x),
+                                float(h0), ctypes.byref(slot)), "tmop_batch_add")
+    return slot.value
+
+
+def tmop_batch_step(b: int) -> int:
+    n = ctypes.c_int()
+    _check(lib().tmop_batch_step(b, ctypes.byref(n)), "tmop_batch_step")
+    return n.value
+
+
+def tmop_batch_state(b: int, slot: int) -> dict:
+    st = MeshState()
+    _check(lib().tmop_batch_state(b, slot, ctypes.byref(st)), "tmop_batch_state")
+    return st.as_dict()
+
+
+def tmop_batch_positions(b: int, slot: int, x_out):
+    _check(lib().tmop_batch_positions(b, slot, _ptr(x_out)), "tmop_batch_positions")
+
+
+def tmop_batch_remove(b: int, slot: int):
+    _check(lib().tmop_batch_remove(b, slot), "tmop_batch_remove")
+
+
+def tmop_batch_mesh_bytes(b: int, num_elems: int, num_nodes: int) -> int:
+    return lib().tmop_batch_mesh_bytes(b, num_elems, num_nodes)
+
+
+def tmop_batch_device_bytes(b: int) -> int:
+    return lib().tmop_batch_device_bytes(b)
+
+
+def tmop_batch_destroy(b: int):
+    lib().tmop_batch_destroy(b)

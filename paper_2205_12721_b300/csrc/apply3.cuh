@@ -27,13 +27,20 @@ struct Apply3Layout {
 template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
 k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
-         const int *__restrict__ stop_iter, int k)
+         const int *__restrict__ stop_iter, int k, BatchArgs BA)
 {
     static_assert(C::D == 3, "3D kernel");
     constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP, NQD = C::NQD, NS = C::NS;
     constexpr int O1 = NI * NI * NQ, O2 = NI * NQ * NQ;
     using L = Apply3Layout<C, RC>;
-    if (stop_iter && *stop_iter < k) return;
+    const void *in = v, *aux = H;
+    void *out = ev;
+    const int *stop = stop_iter;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    v = static_cast<const RV *>(in);
+    H = static_cast<const RC *>(aux);
+    ev = static_cast<RV *>(out);
+    if (stop && *stop < k) return;
     extern __shared__ __align__(16) unsigned char smem[];
     RC *base = reinterpret_cast<RC *>(smem);
     const RC *__restrict__ tab = table_of<RC>(P);
@@ -48,7 +55,7 @@ k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *_
     RC *s1 = su + C::SU;
     RC *s2 = s1 + C::S1;
     int *smap = reinterpret_cast<int *>(base + L::TAB_PAD + C::EPB * L::SLOT) + sl * NP;
-    const int64_t e = (int64_t)blockIdx.x * C::EPB + sl;
+    const int64_t e = tile * C::EPB + sl;
     const bool valid = act && e < P.E;
     if (valid)
         for (int i = t; i < NP; i += C::TPE) smap[i] = P.map[e * NP + i];

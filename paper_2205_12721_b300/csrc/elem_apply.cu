@@ -6,20 +6,20 @@ namespace tmop {
 
 template <class C, class RV, class RC>
 static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
-                             int k, cudaStream_t s)
+                             int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
-    const int64_t nb = grid_of<C>(P.E);
+    const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
     if constexpr (C::D == 3) {
         using L = Apply3Layout<C, RC>;
         cudaError_t e = prepare(k_apply3<C, RV, RC>, L::bytes);
         if (e != cudaSuccess) return e;
-        k_apply3<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+        k_apply3<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k, B);
     } else {
         using L = Layout<C, RC>;
         cudaError_t e = prepare(k_apply<C, RV, RC>, L::bytes);
         if (e != cudaSuccess) return e;
-        k_apply<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k);
+        k_apply<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k, B);
     }
     count_launch();
     return cudaGetLastError();
@@ -27,24 +27,28 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
 
 template <class C>
 static cudaError_t run_apply_any(const ElemParams &P, const void *v, const void *H, void *ev,
-                                 int prec, const int *stop, int k, cudaStream_t s)
+                                 int prec, const int *stop, int k, cudaStream_t s,
+                                 const BatchArgs &B, int64_t nt)
 {
     if (prec == TMOP_FP32)
         return run_apply<C, float, float>(P, static_cast<const float *>(v), static_cast<const float *>(H),
-                                          static_cast<float *>(ev), stop, k, s);
+                                          static_cast<float *>(ev), stop, k, s, B, nt);
     if (prec == TMOP_FP64_NATIVE)
         return run_apply<C, double, double>(P, static_cast<const double *>(v),
                                             static_cast<const double *>(H), static_cast<double *>(ev),
-                                            stop, k, s);
+                                            stop, k, s, B, nt);
     return run_apply<C, double, df>(P, static_cast<const double *>(v), static_cast<const df *>(H),
-                                    static_cast<double *>(ev), stop, k, s);
+                                    static_cast<double *>(ev), stop, k, s, B, nt);
 }
 
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
-                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s)
+                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s,
+                         const BatchArgs *B, int64_t ntiles)
 {
+    const BatchArgs b0 = B ? *B : BatchArgs{};
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_apply_any<Cfg<D_, P_, Q_>>(P, v, H, ev, prec, stop_iter, k, s);
+    case TMOP_KEY(D_, P_, Q_): \
+        return run_apply_any<Cfg<D_, P_, Q_>>(P, v, H, ev, prec, stop_iter, k, s, b0, ntiles);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }

@@ -6,61 +6,65 @@
 namespace tmop {
 
 template <class C, class RS>
-static cudaError_t run_energy(const ElemParams &P, const double *x, double *part, cudaStream_t s)
+static cudaError_t run_energy(const ElemParams &P, const double *x, double *part, cudaStream_t s,
+                              const BatchArgs &B, int64_t ntiles)
 {
     using L = Layout<C, RS>;
-    const int64_t nb = grid_of<C>(P.E);
+    const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
     cudaError_t e = prepare(k_energy<C, RS>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_energy<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, part);
+    k_energy<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, part, B);
     count_launch();
     return cudaGetLastError();
 }
 
 template <class C, class RS>
-static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, cudaStream_t s)
+static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, cudaStream_t s,
+                                const BatchArgs &B, int64_t ntiles)
 {
     using L = Layout<C, RS>;
-    const int64_t nb = grid_of<C>(P.E);
+    const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
     cudaError_t e = prepare(k_gradient<C, RS>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_gradient<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev);
+    k_gradient<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev, B);
     count_launch();
     return cudaGetLastError();
 }
 
 template <class C>
 static cudaError_t run_energy_any(const ElemParams &P, const double *x, double *part, int arith,
-                                  cudaStream_t s)
+                                  cudaStream_t s, const BatchArgs &B, int64_t nt)
 {
-    if (arith == ARITH_NATIVE) return run_energy<C, double>(P, x, part, s);
-    return run_energy<C, df>(P, x, part, s);
+    if (arith == ARITH_NATIVE) return run_energy<C, double>(P, x, part, s, B, nt);
+    return run_energy<C, df>(P, x, part, s, B, nt);
 }
 
 template <class C>
 static cudaError_t run_gradient_any(const ElemParams &P, const double *x, double *ev, int arith,
-                                    cudaStream_t s)
+                                    cudaStream_t s, const BatchArgs &B, int64_t nt)
 {
-    if (arith == ARITH_NATIVE) return run_gradient<C, double>(P, x, ev, s);
-    return run_gradient<C, df>(P, x, ev, s);
+    if (arith == ARITH_NATIVE) return run_gradient<C, double>(P, x, ev, s, B, nt);
+    return run_gradient<C, df>(P, x, ev, s, B, nt);
 }
 
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
-                          int arith, cudaStream_t s)
+                          int arith, cudaStream_t s, const BatchArgs *B, int64_t ntiles)
 {
+    const BatchArgs b0 = B ? *B : BatchArgs{};
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_energy_any<Cfg<D_, P_, Q_>>(P, x, part, arith, s);
+    case TMOP_KEY(D_, P_, Q_): return run_energy_any<Cfg<D_, P_, Q_>>(P, x, part, arith, s, b0, ntiles);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }
 
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
-                            int arith, cudaStream_t s)
+                            int arith, cudaStream_t s, const BatchArgs *B, int64_t ntiles)
 {
+    const BatchArgs b0 = B ? *B : BatchArgs{};
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_gradient_any<Cfg<D_, P_, Q_>>(P, x, ev, arith, s);
+    case TMOP_KEY(D_, P_, Q_): return run_gradient_any<Cfg<D_, P_, Q_>>(P, x, ev, arith, s, b0, ntiles);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }

@@ -30,7 +30,8 @@ struct ElemCtx {
 
 // Stage the tables and the element map; set up the thread's element slot.
 template <class C, class R>
-__device__ __forceinline__ void prologue(const ElemParams &P, unsigned char *smem, ElemCtx<C, R> &c)
+__device__ __forceinline__ void prologue(const ElemParams &P, int64_t tile, unsigned char *smem,
+                                         ElemCtx<C, R> &c)
 {
     using L = Layout<C, R>;
     R *base = reinterpret_cast<R *>(smem);
@@ -52,7 +53,7 @@ __device__ __forceinline__ void prologue(const ElemParams &P, unsigned char *sme
     c.sA = c.s2 + C::S2;
     c.sX = c.sA + C::DD * C::NQD;
     c.smap = reinterpret_cast<int *>(base + L::TAB_PAD + C::EPB * L::SLOT) + sl * C::NP;
-    c.e = (int64_t)blockIdx.x * C::EPB + sl;
+    c.e = tile * C::EPB + sl;
     c.valid = act && c.e < P.E;
     if (c.valid)
         for (int i = c.t; i < C::NP; i += C::TPE) c.smap[i] = P.map[c.e * C::NP + i];
@@ -128,11 +129,17 @@ __device__ __forceinline__ double point_target(const ElemParams &P, const R *sX,
 // RS: arithmetic of the contractions (double, or df = double-float).
 template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
-k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part)
+k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, BatchArgs BA)
 {
+    const void *in = x, *aux = nullptr;
+    void *out = part;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    x = static_cast<const double *>(in);
+    part = static_cast<double *>(out);
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
-    prologue<C, RS>(P, smem, c);
+    prologue<C, RS>(P, tile, smem, c);
     const bool want_x = P.target == TGT_SIZE;
     for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
@@ -170,19 +177,25 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part)
     if (threadIdx.x == 0) {
         double s = 0.0, m = INFINITY;
         for (int i = 0; i < C::NT / 32; ++i) { s += red_s[i]; m = fmin(m, red_m[i]); }
-        part[2 * blockIdx.x] = s;
-        part[2 * blockIdx.x + 1] = m;
+        part[2 * tile] = s;
+        part[2 * tile + 1] = m;
     }
 }
 
 // ---------------------------------------------------------------- gradient
 template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
-k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev)
+k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, BatchArgs BA)
 {
+    const void *in = x, *aux = nullptr;
+    void *out = ev;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    x = static_cast<const double *>(in);
+    ev = static_cast<double *>(out);
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
-    prologue<C, RS>(P, smem, c);
+    prologue<C, RS>(P, tile, smem, c);
     const bool want_x = P.target == TGT_SIZE;
     for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
@@ -221,11 +234,17 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev)
 // ---------------------------------------------------------------- Hessian setup
 template <class C, class RS, class RH>
 __global__ void __launch_bounds__(C::NT)
-k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H)
+k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchArgs BA)
 {
+    const void *in = x, *aux = nullptr;
+    void *out = H;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    x = static_cast<const double *>(in);
+    H = static_cast<RH *>(out);
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
-    prologue<C, RS>(P, smem, c);
+    prologue<C, RS>(P, tile, smem, c);
     const bool want_x = P.target == TGT_SIZE;
     for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
@@ -269,12 +288,19 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H)
 template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
 k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
-        const int *__restrict__ stop_iter, int k)
+        const int *__restrict__ stop_iter, int k, BatchArgs BA)
 {
-    if (stop_iter && *stop_iter < k) return;
+    const void *in = v, *aux = H;
+    void *out = ev;
+    const int *stop = stop_iter;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    v = static_cast<const RV *>(in);
+    H = static_cast<const RC *>(aux);
+    ev = static_cast<RV *>(out);
+    if (stop && *stop < k) return;
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RC> c;
-    prologue<C, RC>(P, smem, c);
+    prologue<C, RC>(P, tile, smem, c);
     for (int a = 0; a < C::D; ++a) forward_component<C, RC, RV>(P, c, v, a, false);
 
     const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
@@ -301,11 +327,17 @@ k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__
 // product d_b w_i d_e w_i factors per direction k into (B or G)(B or G).
 template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
-k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev)
+k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev, BatchArgs BA)
 {
+    const void *in = nullptr, *aux = H;
+    void *out = ev;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    H = static_cast<const RC *>(aux);
+    ev = static_cast<RV *>(out);
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RC> c;
-    prologue<C, RC>(P, smem, c);
+    prologue<C, RC>(P, tile, smem, c);
     __shared__ RC tbl[3][C::NQ * C::NI];          // B*B, B*G, G*G (elementwise)
     for (int i = threadIdx.x; i < C::NQ * C::NI; i += C::NT) {
         tbl[0][i] = prod(c.B[i], c.B[i]);

@@ -50,6 +50,45 @@ struct ElemParams {
     double h0;
 };
 
+// ---- batched launches: one grid over the element tiles of many meshes ----
+// Per-mesh device data of a batch (owned by the batch object).
+struct BMesh {
+    ElemParams P;                       // map, sizes, tables, metric, target, h0
+    const int32_t *csr_ptr, *csr_idx;   // transposed element map
+    const uint8_t *fixed;               // d*Nx or nullptr
+    void *ptr[24];                      // role -> buffer (see enum Role)
+    int64_t ndof;
+    int ntile_e;                        // element tiles (CTAs) of this mesh
+    int nchunk;                         // vector tiles of this mesh
+};
+enum Role {
+    ROLE_NONE = -1, ROLE_X = 0, ROLE_XT, ROLE_G, ROLE_DX, ROLE_H, ROLE_EV64, ROLE_EVR, ROLE_DIAG,
+    ROLE_MINV, ROLE_PART, ROLE_VPART, ROLE_X0, ROLE_KV0 = 12   // ROLE_KV0 .. ROLE_KV0 + 7
+};
+// Launch-level batch arguments; tiles == nullptr means a single-mesh launch.
+struct BatchArgs {
+    const int2 *tiles;          // (mesh, tile) of every CTA
+    const BMesh *meshes;
+    int in, aux, out;           // roles of the kernel's pointer arguments
+    const int *stop;            // per-mesh stop_iter words (stride stop_stride ints)
+    int stop_stride;
+};
+
+// Resolve the CTA's mesh: overwrite P and the pointer arguments, return the tile.
+__device__ __forceinline__ int64_t resolve_tile(ElemParams &P, const BatchArgs &B, const void *&in,
+                                                const void *&aux, void *&out, const int *&stop)
+{
+    if (!B.tiles) return blockIdx.x;
+    const int2 t = B.tiles[blockIdx.x];
+    const BMesh &m = B.meshes[t.x];
+    P = m.P;
+    if (B.in >= 0) in = m.ptr[B.in];
+    if (B.aux >= 0) aux = m.ptr[B.aux];
+    if (B.out >= 0) out = m.ptr[B.out];
+    if (B.stop) stop = B.stop + (int64_t)t.x * B.stop_stride;
+    return t.y;
+}
+
 // Shared-memory layout of one CTA: tables, then EPB element slots, then maps.
 template <class C, class R>
 struct Layout {

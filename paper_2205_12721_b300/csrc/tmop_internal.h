@@ -18,6 +18,7 @@ namespace tmop {
 #define TMOP_KEY(d, p, q) ((d) * 100 + (p) * 10 + (q))
 
 struct ElemParams;
+struct BatchArgs;
 
 // Arithmetic of the FP64-accuracy contractions (energy, gradient, setup).
 enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
@@ -26,16 +27,20 @@ enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
 // error.  nblocks() is the grid size a launch over E elements uses.
 int64_t elem_blocks(int d, int p, int q, int64_t E);
 bool elem_supported(int d, int p, int q);
+// B (optional): batched launch over ntiles (mesh, tile) CTAs; the pointer
+// arguments are then taken from the per-mesh role buffers.
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
-                          int arith, cudaStream_t s);
+                          int arith, cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
-                            int arith, cudaStream_t s);
+                            int arith, cudaStream_t s, const BatchArgs *B = nullptr,
+                            int64_t ntiles = 0);
 cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double *x, void *H,
-                          int prec, cudaStream_t s);
+                          int prec, cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
-                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s);
+                         void *ev, int prec, const int *stop_iter, int k, cudaStream_t s,
+                         const BatchArgs *B = nullptr, int64_t ntiles = 0);
 cudaError_t launch_diag(int d, int p, int q, const ElemParams &P, const void *H, void *ev, int prec,
-                        cudaStream_t s);
+                        cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 
 // Host tables: Gauss-Legendre rule on [0,1], GLL nodes, Lagrange B/G.
 void host_gauss_legendre(int n, double *x, double *w);

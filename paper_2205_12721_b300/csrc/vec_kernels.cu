@@ -7,6 +7,7 @@
 #include <climits>
 #include <cmath>
 
+#include "minres_scalar.cuh"
 #include "tmop_internal.h"
 
 namespace tmop {
@@ -27,12 +28,6 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
     return s;   // valid on thread 0
-}
-
-template <class R>
-__device__ __forceinline__ bool skip(const MinresState *st, int k)
-{
-    return st->stop_iter < k;
 }
 
 // y[dof] = sum over the element entries of the node (fixed order), then the
@@ -149,25 +144,7 @@ __global__ void k_minres_start(const double *__restrict__ part, int nb, MinresSt
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) {
-        const double b1 = sqrt(fmax(s, 0.0));
-        st->beta1 = b1;
-        st->beta = b1;
-        st->beta_old = 0.0;
-        st->alpha = 0.0;
-        st->dbar = 0.0;
-        st->eps = 0.0;
-        st->eps_old = 0.0;
-        st->phibar = b1;
-        st->cs = -1.0;
-        st->sn = 0.0;
-        st->gamma = 1.0;
-        st->delta = 0.0;
-        st->phi = 0.0;
-        st->stop_iter = (b1 > 0.0) ? INT_MAX : 0;
-        st->breakdown = 0;
-        st->iters = 0;
-    }
+    if (threadIdx.x == 0) minres_start_scalars(st, s);
 }
 
 // v = y / beta (first Lanczos vector).
@@ -240,31 +217,7 @@ __global__ void k_fin_beta(const double *__restrict__ part, int nb, MinresState 
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
     s = block_sum(s, sh);
-    if (threadIdx.x != 0) return;
-    st->iters = k;
-    if (s < 0.0) {                       // M^-1 not positive: cannot happen with |diag|
-        st->breakdown = 1;
-        st->stop_iter = k - 1;           // discard this iteration
-        return;
-    }
-    st->beta_old = st->beta;
-    const double beta = sqrt(s);
-    st->beta = beta;
-    const double alpha = st->alpha;
-    st->eps_old = st->eps;
-    const double delta = st->cs * st->dbar + st->sn * alpha;
-    const double gbar = st->sn * st->dbar - st->cs * alpha;
-    st->eps = st->sn * beta;
-    st->dbar = -st->cs * beta;
-    double gamma = sqrt(gbar * gbar + beta * beta);
-    if (gamma < 1e-300) gamma = 1e-300;
-    st->gamma = gamma;
-    st->delta = delta;
-    st->cs = gbar / gamma;
-    st->sn = beta / gamma;
-    st->phi = st->cs * st->phibar;
-    st->phibar = st->sn * st->phibar;
-    if ((!fixed_its && st->phibar <= rtol * st->beta1) || beta == 0.0) st->stop_iter = k;
+    if (threadIdx.x == 0) minres_beta_scalars(st, s, k, rtol, fixed_its);
 }
 
 // wnew = (v - eps_old w1 - delta w2) / gamma; dx += phi wnew; v = ynew / beta.
