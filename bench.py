@@ -303,6 +303,102 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batched(args):
+    """512 independent 3D hex meshes (elements per side U{4..20}, order
+    U{1..4}), metric mu_303 + mu_55 with the size target, grouped by order;
+    time until every mesh has converged (|dF|/|dF0| <= 1e-10 or 40 steps).
+    Batched FP32-mixed and FP64 forms, and the single-mesh FP64 path on a
+    subset of the same meshes."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.batch import TmopBatch
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+
+    work = meshgen.batched_workload(args.n_meshes)
+    out = {"metric": "time-to-converged-mesh (all meshes)", "unit": "s", "higher_is_better": False,
+           "config": {"workload": f"{len(work)} 3D hex meshes, n_e U{{4..20}}, p U{{1..4}}, "
+                                  "mu_303+mu_55, size target W = h0 s(x)^(1/3) I",
+                      "elements": sum(m.num_elems for m, _ in work),
+                      "dofs": sum(m.ndof for m, _ in work)}}
+
+    def batched(prec, subset):
+        groups = {}
+        for j in subset:
+            m, h0 = work[j]
+            groups.setdefault(m.order, []).append(j)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        states = {}
+        steps = 0
+        for p, js in sorted(groups.items()):
+            b = TmopBatch(3, p, capi.METRIC_303_55, target=capi.TARGET_SIZE_FIELD, precision=prec,
+                          max_meshes=len(js), minres_max_it=50, newton_rtol=1e-10, newton_max_it=40)
+            slots = {j: b.add_structured(work[j][0], h0=work[j][1]) for j in js}
+            steps += b.solve(100)
+            for j, s in slots.items():
+                states[j] = b.state(s)
+            b.close()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, states, steps
+
+    def single(subset):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        states = {}
+        for j in subset:
+            m, h0 = work[j]
+            gm = TmopMesh.from_structured(m, capi.METRIC_303_55, target=capi.TARGET_SIZE_FIELD,
+                                          target_h0=h0)
+            x = torch.from_numpy(m.x).cuda()
+            reps = gm.solve(x, max_newton=40, rtol=1e-10, minres_max_it=50)
+            states[j] = reps[-1]
+            gm.close()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, states
+
+    allj = list(range(len(work)))
+    t32, s32, n32 = batched("fp32", allj)
+    t64, s64, n64 = batched("fp64", allj)
+    sub = allj[:args.single_subset]
+    tsub_single, ssingle = single(sub)
+    tsub_b32, _, _ = batched("fp32", sub)
+    tsub_b64, _, _ = batched("fp64", sub)
+    rel = [abs(s32[j]["energy"] - s64[j]["energy"]) / max(abs(s64[j]["energy"]), 1e-300) for j in allj]
+    out.update({"value": t32, "batched_fp32_s": t32, "batched_fp64_s": t64,
+                "subset": {"meshes": len(sub), "single_fp64_s": tsub_single,
+                           "batched_fp32_s": tsub_b32, "batched_fp64_s": tsub_b64},
+                "converged": sum(1 for j in allj if s64[j]["status"] == 0),
+                "newton_its_mean": float(sum(s64[j]["newton_its"] for j in allj) / len(allj)),
+                "fp32_vs_fp64_final_energy_rel_max": max(rel), "batch_steps": n64})
+    return out
+
+
+def run_serving(args):
+    """Poisson stream of mesh-optimisation requests (2D n_e U{8..128} mu_2 or
+    3D n_e U{4..40} mu_302, p U{1..4}); continuous batching under a device
+    memory budget; p50/p99 time from arrival to converged mesh (rtol 1e-6)."""
+    import torch
+    from paper_2205_12721_b300 import meshgen
+    from paper_2205_12721_b300.serve import Server, summarize
+
+    res = {}
+    for rate in args.rates:
+        jobs = meshgen.serving_workload(args.n_jobs, rate=rate, n2=tuple(args.n2), n3=tuple(args.n3))
+        srv = Server(int(args.budget_gb * (1 << 30)), precision=args.precision, newton_rtol=1e-6,
+                     newton_max_it=50, minres_max_it=50)
+        done = srv.run(jobs)
+        srv.close()
+        torch.cuda.synchronize()
+        res[str(rate)] = summarize(done)
+    first = res[str(args.rates[0])]
+    return {"metric": "time-to-converged-mesh p50/p99 under a Poisson request stream", "unit": "s",
+            "higher_is_better": False, "value": first["p50_s"],
+            "config": {"workload": f"{args.n_jobs} requests, 2D n_e U{tuple(args.n2)} mu_2 / "
+                                   f"3D n_e U{tuple(args.n3)} mu_302, p U{{1..4}}, rtol 1e-6",
+                       "budget_gb": args.budget_gb, "precision": args.precision},
+            "by_rate": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,6 +410,14 @@ def main():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--cpu-sample-n", dest="cpu_sample_n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="newton", choices=["newton", "batched", "serving"])
+    ap.add_argument("--n-meshes", dest="n_meshes", type=int, default=512)
+    ap.add_argument("--single-subset", dest="single_subset", type=int, default=32)
+    ap.add_argument("--n-jobs", dest="n_jobs", type=int, default=2000)
+    ap.add_argument("--rates", type=float, nargs="+", default=[10, 50, 200])
+    ap.add_argument("--n2", type=int, nargs=2, default=[8, 128])
+    ap.add_argument("--n3", type=int, nargs=2, default=[4, 40])
+    ap.add_argument("--budget-gb", dest="budget_gb", type=float, default=64.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="override the ncu dram bytes per launch of the apply kernel")
     args = ap.parse_args()
@@ -322,6 +426,11 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.workload != "newton":
+        out = run_batched(args) if args.workload == "batched" else run_serving(args)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

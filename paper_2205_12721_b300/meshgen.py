@@ -185,3 +185,47 @@ def config_mesh(cfg: int, seed: int | None = None, n_e: int | None = None, order
 
 
 CONFIG_METRIC = {1: 2, 2: 302, 3: 303}
+
+
+# ------------------------------------------------------------------ many-mesh workloads
+def batched_workload(n_meshes: int = 512, seed: int = BASE_SEED + 4, n_range=(4, 20),
+                     orders=(1, 2, 3, 4), amp=0.05):
+    """Independent 3D hex meshes of uneven size: elements per side uniform in
+    n_range (inclusive), order uniform in ``orders``; seeded smooth + noise
+    perturbation (amplitude ``amp`` h, noise amp/2 h).  Returns a list of
+    (mesh, h0) with h0 = 1/n_e the size-target scale."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(n_meshes):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        p = int(rng.choice(orders))
+        m = perturb_smooth(structured(3, p, n), seed=seed * 1000 + j, amp_smooth=amp,
+                           amp_noise=amp / 2)
+        out.append((m, 1.0 / n))
+    return out
+
+
+def serving_workload(n_jobs: int = 2000, rate: float = 100.0, seed: int = BASE_SEED + 5,
+                     n2=(8, 128), n3=(4, 40), orders=(1, 2, 3, 4), amp=0.05):
+    """A Poisson stream of mesh-optimisation requests: exponential
+    inter-arrival times at ``rate`` per second; each request is a 2D quad mesh
+    (elements per side uniform in n2, metric mu_2) or a 3D hex mesh (n3,
+    mu_302), order uniform in ``orders``, seeded perturbation.  Returns a list
+    of dicts {id, arrival, dim, order, metric, n, seed}; the mesh is built by
+    ``serving_mesh`` so the list itself stays small."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    jobs = []
+    for j in range(n_jobs):
+        t += float(rng.exponential(1.0 / rate))
+        d = int(rng.choice([2, 3]))
+        lo, hi = (n2 if d == 2 else n3)
+        jobs.append({"id": j, "arrival": t, "dim": d, "order": int(rng.choice(orders)),
+                     "metric": 2 if d == 2 else 302, "n": int(rng.integers(lo, hi + 1)),
+                     "seed": seed * 10000 + j, "amp": amp})
+    return jobs
+
+
+def serving_mesh(job: dict) -> StructuredMesh:
+    m = structured(job["dim"], job["order"], job["n"])
+    return perturb_smooth(m, seed=job["seed"], amp_smooth=job["amp"], amp_noise=job["amp"] / 2)
