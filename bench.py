@@ -112,6 +112,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (the contract's max over ranks)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(n_units: int, rank: int, world: int):
+    """Units (meshes, replicas) of this rank: round robin, no data exchange."""
+    return list(range(rank, n_units, world))
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -177,10 +192,7 @@ def run_ours(args, rank, world, local_rank):
             [("energy", capi.K_ENERGY), ("gradient", capi.K_GRADIENT), ("hsetup", capi.K_HSETUP),
              ("apply", capi.K_APPLY), ("diag", capi.K_DIAG), ("assemble", capi.K_ASSEMBLE)]}
     capi.tmop_profile_enable(gm.ctx, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     applies = MINRES_ITS
     value = world * m.ndof * applies / (ms * 1e-3) / 1e9
 
@@ -200,10 +212,7 @@ def run_ours(args, rank, world, local_rank):
             xout.copy_(x, non_blocking=True)
         stream.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e = {"value": world * m.ndof * applies / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(xout.numel() * 8)}
 
