@@ -265,9 +265,22 @@ def run_ours(args, rank, world, local_rank):
                    "energy": reps[-1]["energy"], "energy_new": reps[-1]["energy_new"]},
         "clocks": clk.summary(),
     }
+    gm.close()
+    if args.variants and rank == 0:
+        # the same step in the other precision modes (reported beside the value)
+        out["variants"] = {}
+        for prec in args.variants:
+            if prec == args.precision:
+                continue
+            sub = argparse.Namespace(**vars(args))
+            sub.precision, sub.variants, sub.no_cpu_baseline = prec, [], True
+            sub.traffic = TRAFFIC_BYTES.get(prec) if (args.n_e == 48 and args.order == 3) else None
+            v = run_ours(sub, 0, 1, local_rank)
+            out["variants"][prec] = {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                                     "dtype": v["dtype"], "roofline": v["roofline"],
+                                     "kernel_ms": v["kernel_ms"]}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
-    gm.close()
     return out
 
 
@@ -419,6 +432,8 @@ def main():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--cpu-sample-n", dest="cpu_sample_n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", nargs="*", default=["fp32"],
+                    help="other precisions timed after the main run (rank 0)")
     ap.add_argument("--workload", default="newton", choices=["newton", "batched", "serving"])
     ap.add_argument("--n-meshes", dest="n_meshes", type=int, default=512)
     ap.add_argument("--single-subset", dest="single_subset", type=int, default=32)

@@ -587,12 +587,11 @@ BatchArgs bargs(const tmop_batch *b, int in, int aux, int out, bool stop)
 tmop_status eval_fg(tmop_batch *b, int xr, int which)
 {
     ElemParams P0{};
-    BatchArgs a = bargs(b, xr, -1, ROLE_PART, false);
-    BCK(launch_energy(b->d, b->p, b->nq, P0, nullptr, nullptr, b->arith, b->stream, &a, b->nt_e));
+    // fused pass: energy / min det partials (aux role) and the element gradient
+    BatchArgs a = bargs(b, xr, ROLE_PART, ROLE_EV64, false);
+    BCK(launch_gradient(b->d, b->p, b->nq, P0, nullptr, nullptr, b->arith, b->stream, &a, b->nt_e));
     b_energy_final<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, which);
     count_launch();
-    a = bargs(b, xr, -1, ROLE_EV64, false);
-    BCK(launch_gradient(b->d, b->p, b->nq, P0, nullptr, nullptr, b->arith, b->stream, &a, b->nt_e));
     b_assemble<double, double><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EV64, ROLE_G,
                                                                 0, b->d, b->np, nullptr, 0);
     b_dot<double, double><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, ROLE_G, ROLE_G);

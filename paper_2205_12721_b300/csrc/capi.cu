@@ -234,6 +234,31 @@ tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
     return TMOP_OK;
 }
 
+// Fused energy + min det + gradient (one forward pass): g on the device,
+// F and min det on the host (synchronises).
+tmop_status energy_grad_sync(tmop_ctx *c, const double *x, double *g, double *F, double *md)
+{
+    const ElemParams P = c->params();
+    const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
+    TRY(timed(c, TMOP_K_GRADIENT, "energy+gradient kernel", [&] {
+        return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->arith, c->stream, nullptr, 0,
+                               c->part);
+    }));
+    CK(launch_finalize_energy(c->part, nb, c->scal, c->stream));
+    TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
+        return launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 0,
+                               c->Nx, c->d, c->ENP, g, TMOP_FP64, nullptr, 0, c->stream);
+    }));
+    TRY(read_scalars(c, 2));
+    *md = c->hscal[1];
+    if (!(c->hscal[1] > 0.0) && c->E > 0) {
+        *F = INFINITY;
+        return fail(TMOP_ERR_INVERTED, "det(A) <= 0 at some quadrature point");
+    }
+    *F = c->hscal[0];
+    return TMOP_OK;
+}
+
 // ||a||_2 for an FP64 vector (synchronises).
 tmop_status norm_sync(tmop_ctx *c, const double *a, double *out)
 {
@@ -571,11 +596,9 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         return st;
     };
     double F0 = 0, md0 = 0;
-    tmop_status st = energy_sync(c, x, &F0, &md0);
+    tmop_status st = energy_grad_sync(c, x, c->g, &F0, &md0);
     r.energy = F0;
     r.min_det = md0;
-    if (st != TMOP_OK) return finish(st);
-    st = gradient_async(c, x, c->g);
     if (st != TMOP_OK) return finish(st);
     double g0 = 0;
     st = norm_sync(c, c->g, &g0);
@@ -604,11 +627,10 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         cudaError_t e = launch_trial(x, c->dx, alpha, c->ndof, c->xt, c->stream);
         if (e != cudaSuccess) return finish(cuda_fail(e, "trial"));
         double F1 = 0, md1 = 0;
-        st = energy_sync(c, c->xt, &F1, &md1);
+        st = energy_grad_sync(c, c->xt, c->g, &F1, &md1);
         if (st == TMOP_ERR_INVERTED) continue;            // det A(x+) > 0 required
         if (st != TMOP_OK) return finish(st);
         if (!(F1 < o.ls_factor * F0)) continue;           // energy test
-        if ((st = gradient_async(c, c->xt, c->g)) != TMOP_OK) return finish(st);
         double g1 = 0;
         if ((st = norm_sync(c, c->g, &g1)) != TMOP_OK) return finish(st);
         if (!(g1 < o.ls_factor * g0)) continue;           // gradient test

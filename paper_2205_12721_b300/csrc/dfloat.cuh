@@ -14,11 +14,67 @@
 
 namespace tmop {
 
+// Bit-level conversions between double and float pairs that use only the
+// integer and FP32 pipes (B300's FP64 pipe, which also executes the F2F
+// conversions to and from double, is the scarce resource).  Values outside
+// the range where both words are normal floats take the plain conversion.
+__host__ __device__ __forceinline__ unsigned long long dbits(double v)
+{
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long b;
+    __builtin_memcpy(&b, &v, 8);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double from_dbits(unsigned long long b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double v;
+    __builtin_memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned fbits(float v)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(v);
+#else
+    unsigned b;
+    __builtin_memcpy(&b, &v, 4);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ float from_fbits(unsigned b)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float v;
+    __builtin_memcpy(&v, &b, 4);
+    return v;
+#endif
+}
+
+// float -> double by assembling the bits (exact for normal floats and zero)
+__host__ __device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = fbits(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;            // zero, subnormal, inf, nan
+    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+    return from_dbits(s | ((unsigned long long)(e - 127u + 1023u) << 52) |
+                      ((unsigned long long)(b & 0x7FFFFFu) << 29));
+}
+
 struct df {
     float h, l;
     df() = default;
     __host__ __device__ __forceinline__ df(float hi, float lo) : h(hi), l(lo) {}
-    // exact up to the 48-bit significand: h = rn(v), l = rn(v - h)
+    // h = rn(v), l = rn(v - h): conversions on the FP64 pipe
     __host__ __device__ __forceinline__ df(double v)
     {
         h = (float)v;
@@ -29,6 +85,30 @@ struct df {
         return (double)h + (double)l;
     }
 };
+
+// The same split built from the bits on the integer/FP32 pipes, for kernels
+// whose FP64 pipe is the bottleneck: h = v rounded to 24 significant bits,
+// l = the signed remainder (29 bits rounded to 24), |l| <= ulp(h)/2.
+__host__ __device__ __forceinline__ df df_bits(double v)
+{
+    const unsigned long long b = dbits(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int fe = e - 1023 + 127;                      // float exponent of h
+    const int se = e - 1075 + 127;                      // float exponent of 2^(e-1075)
+    if (fe <= 0 || fe >= 254 || se <= 0) return df(v);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    unsigned hb = sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFull);
+    int r = (int)(b & 0x1FFFFFFFull);                   // dropped 29 fraction bits
+    if (r >= (1 << 28)) {                               // round the magnitude up
+        hb += 1u;
+        r -= (1 << 29);
+    }
+    const float lv = (float)r * from_fbits((unsigned)se << 23);
+    return df(from_fbits(hb), sign ? -lv : lv);
+}
+
+// double from a float pair on the integer pipe plus one FP64 add.
+__host__ __device__ __forceinline__ double d_bits(const df &x) { return f2d_bits(x.h) + f2d_bits(x.l); }
 
 // An unnormalised product p + e (|e| small relative to |p|).
 struct dprod {
@@ -110,6 +190,12 @@ __device__ __forceinline__ df to_df(const df &a) { return a; }
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return (double)v; }
 __device__ __forceinline__ double to_d(const df &v) { return (double)v; }
+// ... and the bit-level variants for FP64-pipe-bound kernels
+__device__ __forceinline__ double to_db(double v) { return v; }
+__device__ __forceinline__ double to_db(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double to_db(const df &v) { return d_bits(v); }
+template <class R> __device__ __forceinline__ R from_db(double v) { return R(v); }
+template <> __device__ __forceinline__ df from_db<df>(double v) { return df_bits(v); }
 
 template <class R>
 __device__ __forceinline__ R from_d(double v) { return (R)v; }

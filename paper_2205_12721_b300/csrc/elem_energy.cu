@@ -20,15 +20,15 @@ static cudaError_t run_energy(const ElemParams &P, const double *x, double *part
 }
 
 template <class C, class RS>
-static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, cudaStream_t s,
-                                const BatchArgs &B, int64_t ntiles)
+static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, double *part,
+                                cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
     using L = Layout<C, RS>;
     const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
     cudaError_t e = prepare(k_gradient<C, RS>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_gradient<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev, B);
+    k_gradient<C, RS><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, ev, part, B);
     count_launch();
     return cudaGetLastError();
 }
@@ -42,11 +42,11 @@ static cudaError_t run_energy_any(const ElemParams &P, const double *x, double *
 }
 
 template <class C>
-static cudaError_t run_gradient_any(const ElemParams &P, const double *x, double *ev, int arith,
-                                    cudaStream_t s, const BatchArgs &B, int64_t nt)
+static cudaError_t run_gradient_any(const ElemParams &P, const double *x, double *ev, double *part,
+                                    int arith, cudaStream_t s, const BatchArgs &B, int64_t nt)
 {
-    if (arith == ARITH_NATIVE) return run_gradient<C, double>(P, x, ev, s, B, nt);
-    return run_gradient<C, df>(P, x, ev, s, B, nt);
+    if (arith == ARITH_NATIVE) return run_gradient<C, double>(P, x, ev, part, s, B, nt);
+    return run_gradient<C, df>(P, x, ev, part, s, B, nt);
 }
 
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
@@ -60,11 +60,13 @@ cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double
 }
 
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
-                            int arith, cudaStream_t s, const BatchArgs *B, int64_t ntiles)
+                            int arith, cudaStream_t s, const BatchArgs *B, int64_t ntiles,
+                            double *part)
 {
     const BatchArgs b0 = B ? *B : BatchArgs{};
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return run_gradient_any<Cfg<D_, P_, Q_>>(P, x, ev, arith, s, b0, ntiles);
+    case TMOP_KEY(D_, P_, Q_): \
+        return run_gradient_any<Cfg<D_, P_, Q_>>(P, x, ev, part, arith, s, b0, ntiles);
     TMOP_SWITCH(d, p, q, CASE)
 #undef CASE
 }

@@ -112,7 +112,7 @@ __device__ __forceinline__ void for_my_points(int tx, int ty, bool valid, F &&f)
 template <class C, class R>
 __device__ __forceinline__ double point_weight(const R *w, int tx, int ty, int q3)
 {
-    return C::D == 3 ? to_d(w[tx]) * to_d(w[ty]) * to_d(w[q3]) : to_d(w[tx]) * to_d(w[ty]);
+    return C::D == 3 ? to_db(w[tx]) * to_db(w[ty]) * to_db(w[q3]) : to_db(w[tx]) * to_db(w[ty]);
 }
 
 template <class C, class R>
@@ -121,8 +121,30 @@ __device__ __forceinline__ double point_target(const ElemParams &P, const R *sX,
     double xq[3] = {0, 0, 0};
     if (P.target == TGT_SIZE)
 #pragma unroll
-        for (int k = 0; k < C::D; ++k) xq[k] = to_d(sX[k * C::NQD + q]);
+        for (int k = 0; k < C::D; ++k) xq[k] = to_db(sX[k * C::NQD + q]);
     return target_scale<C::D>(P.target, P.h0, xq);
+}
+
+// Deterministic CTA reduction of (energy sum, min det) into part[2 tile + {0,1}]:
+// warps by shuffles, then warp results in order.  Called by all threads.
+template <class C>
+__device__ __forceinline__ void cta_energy_reduce(double esum, double emin, double *part, int64_t tile)
+{
+    __shared__ double red_s[C::NT / 32], red_m[C::NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        esum += __shfl_down_sync(0xffffffffu, esum, o);
+        emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red_s[wid] = esum; red_m[wid] = emin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, m = INFINITY;
+        for (int i = 0; i < C::NT / 32; ++i) { s += red_s[i]; m = fmin(m, red_m[i]); }
+        part[2 * tile] = s;
+        part[2 * tile + 1] = m;
+    }
 }
 
 // ---------------------------------------------------------------- energy
@@ -153,7 +175,7 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
         const double detA = tau * wd;
@@ -164,41 +186,30 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
         }
     });
 
-    // deterministic CTA reduction: warps, then warp 0
-    __shared__ double red_s[C::NT / 32], red_m[C::NT / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        esum += __shfl_down_sync(0xffffffffu, esum, o);
-        emin = fmin(emin, __shfl_down_sync(0xffffffffu, emin, o));
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { red_s[wid] = esum; red_m[wid] = emin; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0, m = INFINITY;
-        for (int i = 0; i < C::NT / 32; ++i) { s += red_s[i]; m = fmin(m, red_m[i]); }
-        part[2 * tile] = s;
-        part[2 * tile + 1] = m;
-    }
+    cta_energy_reduce<C>(esum, emin, part, tile);
 }
 
 // ---------------------------------------------------------------- gradient
 template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
-k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, BatchArgs BA)
+k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, double *part,
+           BatchArgs BA)
 {
-    const void *in = x, *aux = nullptr;
+    // part != nullptr: also the energy and min det partials (fused pass)
+    const void *in = x, *aux = part;
     void *out = ev;
     const int *stop = nullptr;
     const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
     x = static_cast<const double *>(in);
     ev = static_cast<double *>(out);
+    part = const_cast<double *>(static_cast<const double *>(aux));
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
     prologue<C, RS>(P, tile, smem, c);
     const bool want_x = P.target == TGT_SIZE;
     for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
 
+    double esum = 0.0, emin = INFINITY;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
         const double ws = point_target<C>(P, c.sX, q);
@@ -208,25 +219,27 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
+        emin = fmin(emin, tau * wd);
         if (!(tau > 0.0)) {                               // inverted points contribute 0
 #pragma unroll
             for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0);
             return;
         }
         Inv v;
-        metric_scalars(P.metric, I1, tau, I2, v);
+        esum += cq * metric_scalars(P.metric, I1, tau, I2, v);
         if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
         const double sc = cq * iws;
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) {
             double pr = v.f1 * 2.0 * T[r] + v.ft * Cf[r];
             if (C::D == 3 && v.f2 != 0.0) pr += v.f2 * g2[r];
-            c.sA[r * C::NQD + q] = RS(sc * pr);
+            c.sA[r * C::NQD + q] = from_db<RS>(sc * pr);
         }
     });
+    if (part) cta_energy_reduce<C>(esum, emin, part, tile);   // part is uniform per launch
     __syncthreads();
     for (int a = 0; a < C::D; ++a) backward_component<C, RS, double>(P, c, ev, a);
 }
@@ -258,7 +271,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_d(c.sA[r * C::NQD + q]) * iws;
+        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
         if (!(tau > 0.0)) {                               // inverted points store 0
@@ -275,7 +288,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
 #pragma unroll
             for (int s = r; s < C::DD; ++s)
                 He[pidx<C::DD>(r, s) * C::NQD + q] =
-                    RH(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+                    from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
     });
 }
 

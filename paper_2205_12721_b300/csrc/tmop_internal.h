@@ -31,9 +31,10 @@ bool elem_supported(int d, int p, int q);
 // arguments are then taken from the per-mesh role buffers.
 cudaError_t launch_energy(int d, int p, int q, const ElemParams &P, const double *x, double *part,
                           int arith, cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
+// part != nullptr (or a batch aux role): fused energy + min det partials.
 cudaError_t launch_gradient(int d, int p, int q, const ElemParams &P, const double *x, double *ev,
                             int arith, cudaStream_t s, const BatchArgs *B = nullptr,
-                            int64_t ntiles = 0);
+                            int64_t ntiles = 0, double *part = nullptr);
 cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double *x, void *H,
                           int prec, cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
