@@ -395,6 +395,91 @@ def run_batched(args):
     return out
 
 
+def run_sweep(args):
+    """Hessian-action throughput versus problem size (the paper's Sec. 4.1
+    throughput methodology: one Newton iteration's worth of actions on the
+    initial perturbed mesh): 3D, p = 1..4, n_q = p+1 and p+2, n_e in a size
+    ladder; FP64-class and FP32.  GDOF/s = DOFs / mean action time, and the
+    fraction of the measured HBM bandwidth of the action's algorithmic
+    bytes."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    hbm = measured_peaks().get("hbm_gbs")
+    rows = []
+    for p in (1, 2, 3, 4):
+        for n in args.sweep_sizes:
+            if (n * p + 1) ** 3 * 3 > 40e6:
+                continue
+            m = meshgen.config_mesh(3, n_e=n, order=p)
+            for dq in (1, 2):
+                nq = p + dq
+                for prec in args.sweep_precisions:
+                    rsz = 4 if prec == "fp32" else 8
+                    gm = TmopMesh.from_structured(m, capi.METRIC_303, nq1d=nq, precision=prec)
+                    x = torch.from_numpy(m.x).cuda()
+                    gm.hessian_setup(x)
+                    v = torch.randn(m.ndof, dtype=gm.rdtype, device="cuda")
+                    y = torch.empty_like(v)
+                    for _ in range(3):
+                        gm.hessian_apply(v, y)
+                    capi.tmop_profile_enable(gm.ctx, True)
+                    reps = 20
+                    for _ in range(reps):
+                        gm.hessian_apply(v, y)
+                    ms, nl = capi.tmop_profile_read(gm.ctx, capi.K_APPLY)
+                    ams, _ = capi.tmop_profile_read(gm.ctx, capi.K_ASSEMBLE)
+                    gm.close()
+                    t = ms / nl
+                    byts = bytes_apply_per_elem(3, p + 1, nq, 45, rsz) * m.num_elems
+                    rows.append({"precision": prec, "p": p, "nq": nq, "n_e": n, "dofs": m.ndof,
+                                 "apply_ms": t, "assemble_ms": ams / nl,
+                                 "gdofs_kernel": m.ndof / (t * 1e-3) / 1e9,
+                                 "gdofs_with_assembly": m.ndof / ((t + ams / nl) * 1e-3) / 1e9,
+                                 "hbm_frac": (byts / (t * 1e-3) / 1e9 / hbm) if hbm else None})
+                    del x, v, y
+                    torch.cuda.empty_cache()
+    return {"metric": "Hessian-apply GDOF/s vs size (3D hex, p=1..4)", "unit": "GDOF/s",
+            "higher_is_better": True, "value": max(r["gdofs_kernel"] for r in rows), "rows": rows}
+
+
+def run_solve(args):
+    """Time to converged mesh of the single-mesh configurations: 2D 8x8 Q2
+    (mu_2, exactly 10 Newton steps, MINRES rtol 1e-8) and 3D 24^3 Q2 (mu_302,
+    |dF|/|dF0| <= 1e-10, FP64-class vs FP32-mixed)."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    out = {"metric": "time-to-converged-mesh", "unit": "s", "higher_is_better": False, "runs": {}}
+    cases = [("2d_8x8_q2_mu2", 1, capi.METRIC_2, "fp64", dict(max_newton=10, rtol=0.0)),
+             ("3d_24cube_q2_mu302_fp64", 2, capi.METRIC_302, "fp64", dict(max_newton=100, rtol=1e-10)),
+             ("3d_24cube_q2_mu302_fp32", 2, capi.METRIC_302, "fp32", dict(max_newton=100, rtol=1e-10))]
+    for name, cfg, metric, prec, kw in cases:
+        m = meshgen.config_mesh(cfg)
+        res = []
+        for rep in range(2):                              # first run warms up
+            gm = TmopMesh.from_structured(m, metric, precision=prec)
+            x = torch.from_numpy(m.x).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = gm.solve(x, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st, F, md = gm.energy(x)
+            gm.close()
+            res = {"seconds": dt, "newton_its": len(reps),
+                   "minres_its": sum(r["minres_iters"] for r in reps),
+                   "energy0": reps[0]["energy"], "energy": F,
+                   "grad_ratio": reps[-1]["grad_norm_new"] / reps[0]["grad_norm"],
+                   "status": reps[-1]["status"], "dofs": m.ndof}
+        out["runs"][name] = res
+    f64 = out["runs"]["3d_24cube_q2_mu302_fp64"]["energy"]
+    f32 = out["runs"]["3d_24cube_q2_mu302_fp32"]["energy"]
+    out["fp32_vs_fp64_final_energy_rel"] = abs(f32 - f64) / max(abs(f64), 1e-300)
+    out["value"] = out["runs"]["3d_24cube_q2_mu302_fp64"]["seconds"]
+    return out
+
+
 def run_serving(args):
     """Poisson stream of mesh-optimisation requests (2D n_e U{8..128} mu_2 or
     3D n_e U{4..40} mu_302, p U{1..4}); continuous batching under a device
@@ -434,7 +519,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", nargs="*", default=["fp32"],
                     help="other precisions timed after the main run (rank 0)")
-    ap.add_argument("--workload", default="newton", choices=["newton", "batched", "serving"])
+    ap.add_argument("--workload", default="newton",
+                    choices=["newton", "batched", "serving", "sweep", "solve"])
+    ap.add_argument("--sweep-sizes", dest="sweep_sizes", type=int, nargs="+",
+                    default=[4, 8, 16, 24, 32, 48])
+    ap.add_argument("--sweep-precisions", dest="sweep_precisions", nargs="+", default=["fp64", "fp32"])
     ap.add_argument("--n-meshes", dest="n_meshes", type=int, default=512)
     ap.add_argument("--single-subset", dest="single_subset", type=int, default=32)
     ap.add_argument("--n-jobs", dest="n_jobs", type=int, default=2000)
@@ -451,7 +540,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.workload != "newton":
-        out = run_batched(args) if args.workload == "batched" else run_serving(args)
+        out = {"batched": run_batched, "serving": run_serving, "sweep": run_sweep,
+               "solve": run_solve}[args.workload](args)
         if rank == 0:
             print(json.dumps(out))
         return

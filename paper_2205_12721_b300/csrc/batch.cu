@@ -131,12 +131,18 @@ __global__ void b_assemble(const BMesh *M, const int2 *tiles, int ev_role, int o
     RO *out = rp<RO>(bm, out_role);
     const int64_t ENP = bm.P.E * NP;
     const int b = bm.csr_ptr[n], e = bm.csr_ptr[n + 1];
-    for (int a = 0; a < D; ++a) {
-        double s = 0.0;
-        for (int j = b; j < e; ++j) s += (double)ev[a * ENP + bm.csr_idx[j]];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int j = b; j < e; ++j) {
+        const int64_t t = bm.csr_idx[j];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a < D) s[a] += (double)ev[a * ENP + t];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) break;
         const int64_t dof = a * Nx + n;
-        if (bm.fixed && bm.fixed[dof]) s = (mode == 2) ? 1.0 : 0.0;
-        out[dof] = (RO)s;
+        out[dof] = (RO)((bm.fixed && bm.fixed[dof]) ? ((mode == 2) ? 1.0 : 0.0) : s[a]);
     }
 }
 

@@ -42,12 +42,21 @@ __global__ void k_assemble(const RI *__restrict__ ev, const int32_t *__restrict_
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Nx) return;
     const int b = ptr[n], e = ptr[n + 1];
-    for (int a = 0; a < D; ++a) {
-        double s = 0.0;
-        for (int j = b; j < e; ++j) s += (double)ev[a * ENP + idx[j]];
+    // entries in fixed order; the D component loads of an entry are independent
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int j = b; j < e; ++j) {
+        const int64_t t = __ldg(idx + j);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a < D) s[a] += (double)__ldg(ev + a * ENP + t);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) break;
         const int64_t dof = a * Nx + n;
-        if (fixed && fixed[dof]) s = (mode == 0) ? 0.0 : (mode == 1 ? (vfix ? (double)vfix[dof] : 0.0) : 1.0);
-        out[dof] = (RO)s;
+        double r = s[a];
+        if (fixed && fixed[dof]) r = (mode == 0) ? 0.0 : (mode == 1 ? (vfix ? (double)vfix[dof] : 0.0) : 1.0);
+        out[dof] = (RO)r;
     }
 }
 
