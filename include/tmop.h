@@ -86,7 +86,7 @@ enum { TMOP_FP64 = 0, TMOP_FP32 = 1, TMOP_FP64_NATIVE = 2 };
 typedef struct {
     int dim;             /* 2 or 3 */
     int order;           /* p, 1..4 */
-    int nq1d;            /* quadrature points per direction: p+1 or p+2 */
+    int nq1d;            /* quadrature points per direction: p+1, p+2, or 9 (3D) */
     int64_t num_elems;
     int64_t num_nodes;   /* N_x */
     int metric;          /* TMOP_METRIC_* valid for dim */

@@ -404,7 +404,7 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     if (D.dim != 2 && D.dim != 3) return fail(TMOP_ERR_ARG, "dim must be 2 or 3");
     if (D.order < 1 || D.order > 4) return fail(TMOP_ERR_UNSUPPORTED, "order must be 1..4");
     if (!elem_supported(D.dim, D.order, D.nq1d))
-        return fail(TMOP_ERR_UNSUPPORTED, "nq1d must be order+1 or order+2");
+        return fail(TMOP_ERR_UNSUPPORTED, "nq1d must be order+1, order+2 (or 9 in 3D)");
     if (D.num_elems < 0 || D.num_nodes <= 0) return fail(TMOP_ERR_ARG, "bad mesh sizes");
     if (!metric_ok(D.metric, D.dim)) return fail(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
     if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)

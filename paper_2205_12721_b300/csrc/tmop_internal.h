@@ -11,10 +11,12 @@
 
 namespace tmop {
 
-// Supported (dim, order, nq1d) triples: every p in 1..4 with nq1d in {p+1, p+2}.
+// Supported (dim, order, nq1d) triples: every p in 1..4 with nq1d in {p+1, p+2},
+// and in 3D also nq1d = 9 (the 9^3-point rule of the paper's Kershaw runs).
 #define TMOP_CONFIGS(X)                                                                    \
     X(2, 1, 2) X(2, 1, 3) X(2, 2, 3) X(2, 2, 4) X(2, 3, 4) X(2, 3, 5) X(2, 4, 5) X(2, 4, 6) \
-    X(3, 1, 2) X(3, 1, 3) X(3, 2, 3) X(3, 2, 4) X(3, 3, 4) X(3, 3, 5) X(3, 4, 5) X(3, 4, 6)
+    X(3, 1, 2) X(3, 1, 3) X(3, 2, 3) X(3, 2, 4) X(3, 3, 4) X(3, 3, 5) X(3, 4, 5) X(3, 4, 6) \
+    X(3, 1, 9) X(3, 2, 9) X(3, 3, 9) X(3, 4, 9)
 #define TMOP_KEY(d, p, q) ((d) * 100 + (p) * 10 + (q))
 
 struct ElemParams;

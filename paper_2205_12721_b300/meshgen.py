@@ -229,3 +229,60 @@ def serving_workload(n_jobs: int = 2000, rate: float = 100.0, seed: int = BASE_S
 def serving_mesh(job: dict) -> StructuredMesh:
     m = structured(job["dim"], job["order"], job["n"])
     return perturb_smooth(m, seed=job["seed"], amp_smooth=job["amp"], amp_noise=job["amp"] / 2)
+
+
+# ------------------------------------------------------------------ Kershaw benchmark mesh
+def _kershaw_right(eps, t):
+    """1D map of the right end: slope (2 - eps) up to 1/2, slope eps after."""
+    return np.where(t <= 0.5, (2.0 - eps) * t, 1.0 + eps * (t - 1.0))
+
+
+def _kershaw_left(eps, t):
+    return 1.0 - _kershaw_right(eps, 1.0 - t)
+
+
+def _kershaw_blend(a, b, s):
+    """a -> b with the quintic smoothstep 10s^3 - 15s^4 + 6s^5, s clamped to [0,1]."""
+    s = np.clip(s, 0.0, 1.0)
+    w = s * s * s * (10.0 + s * (6.0 * s - 15.0))
+    return a + (b - a) * w
+
+
+def kershaw_map(X, eps_y, eps_z):
+    """The Kershaw deformation of [0,1]^3 (paper Sec. 4.1 and its appendix):
+    x is kept; the unit x-range is cut into 6 layers; in the first layer y, z
+    follow the left-end 1D map, in the last the right-end map, and the middle
+    layers blend between them with a quintic smoothstep (layers 1 and 4 go
+    left -> right, layers 2-3 go right -> left over two layers).  X has shape
+    (3, n); returns the deformed points."""
+    x, y, z = X
+    layer = np.minimum(np.floor(6.0 * x), 6).astype(int)
+    lam = 6.0 * x - layer
+    out = np.empty_like(X)
+    out[0] = x
+    for k, (t, eps) in enumerate(((y, eps_y), (z, eps_z)), start=1):
+        L, R = _kershaw_left(eps, t), _kershaw_right(eps, t)
+        v = np.where(layer == 0, L, R)                       # layers 0 and >= 5
+        v = np.where((layer == 1) | (layer == 4), _kershaw_blend(L, R, lam), v)
+        v = np.where(layer == 2, _kershaw_blend(R, L, lam / 2.0), v)
+        v = np.where(layer == 3, _kershaw_blend(R, L, (1.0 + lam) / 2.0), v)
+        out[k] = v
+    return out
+
+
+def kershaw(order: int, n=(24, 24, 24), eps_y: float = 0.3, eps_z: float = 0.3) -> StructuredMesh:
+    """Kershaw mesh: a uniform Q_order mesh of [0,1]^3 (n_x divisible by 6,
+    n_y, n_z even) with every node moved by ``kershaw_map``.  Boundary nodes
+    keep only their normal component fixed, so they can slide within their
+    faces toward the uniform optimum the paper states."""
+    if n[0] % 6 or n[1] % 2 or n[2] % 2:
+        raise ValueError("n_x must be a multiple of 6 and n_y, n_z even")
+    m = structured(3, order, n)
+    Nx = m.num_nodes
+    X = m.x.reshape(3, Nx)
+    m.x = kershaw_map(X, eps_y, eps_z).reshape(-1).copy()
+    fixed = np.zeros((3, Nx), dtype=np.uint8)
+    for a in range(3):
+        fixed[a] = (np.abs(X[a]) < 1e-14) | (np.abs(X[a] - 1.0) < 1e-14)
+    m.fixed = fixed.reshape(-1).copy()
+    return m
