@@ -480,6 +480,46 @@ def run_solve(args):
     return out
 
 
+def run_kershaw(args):
+    """The paper's Kershaw benchmark (Sec. 4.1): 24^3 hexes, eps_y = eps_z =
+    0.3, 9^3 quadrature points, mu_303, Jacobi-MINRES with at most 50
+    iterations per Newton step, Newton until |dF|/|dF0| <= 1e-10; boundary
+    nodes slide in their faces.  Time to solution per order p, FP64 class and
+    FP32 mixed, beside the paper's GPU numbers (4 V100, context)."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    paper = {1: 0.4, 2: 0.9, 3: 3.9, 4: 8.5}          # GPU PA + Jacobi, seconds (Sec. 4.1 table)
+    rows = []
+    for p in args.kershaw_orders:
+        m = meshgen.kershaw(p, (args.kershaw_n,) * 3, 0.3, 0.3)
+        u = meshgen.structured(3, p, (args.kershaw_n,) * 3)
+        for prec in args.kershaw_precisions:
+            gm = TmopMesh.from_structured(m, capi.METRIC_303, nq1d=args.kershaw_nq, precision=prec)
+            x = torch.from_numpy(m.x).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = gm.solve(x, max_newton=200, rtol=1e-10, minres_rtol=args.kershaw_minres_rtol,
+                            minres_max_it=50)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            gm.close()
+            rows.append({"p": p, "precision": prec, "dofs": m.ndof, "seconds": dt,
+                         "newton_its": len(reps),
+                         "minres_its": sum(r["minres_iters"] for r in reps),
+                         "status": reps[-1]["status"],
+                         "grad_ratio": reps[-1]["grad_norm_new"] / reps[0]["grad_norm"],
+                         "max_dist_to_uniform_over_h":
+                             float((x.cpu().numpy() - u.x).__abs__().max() * args.kershaw_n),
+                         "paper_gpu_s_4xV100": paper.get(p)})
+    return {"metric": "Kershaw time to solution", "unit": "s", "higher_is_better": False,
+            "value": rows[0]["seconds"],
+            "config": {"workload": f"Kershaw {args.kershaw_n}^3, eps 0.3, {args.kershaw_nq}^3 points, "
+                                   f"mu_303, MINRES <= 50 (rtol {args.kershaw_minres_rtol:g}) + Jacobi, "
+                                   "Newton to 1e-10"},
+            "rows": rows}
+
+
 def run_serving(args):
     """Poisson stream of mesh-optimisation requests (2D n_e U{8..128} mu_2 or
     3D n_e U{4..40} mu_302, p U{1..4}); continuous batching under a device
@@ -520,7 +560,13 @@ def main():
     ap.add_argument("--variants", nargs="*", default=["fp32"],
                     help="other precisions timed after the main run (rank 0)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "batched", "serving", "sweep", "solve"])
+                    choices=["newton", "batched", "serving", "sweep", "solve", "kershaw"])
+    ap.add_argument("--kershaw-orders", dest="kershaw_orders", type=int, nargs="+", default=[1, 2, 3, 4])
+    ap.add_argument("--kershaw-precisions", dest="kershaw_precisions", nargs="+",
+                    default=["fp64", "fp32"])
+    ap.add_argument("--kershaw-n", dest="kershaw_n", type=int, default=24)
+    ap.add_argument("--kershaw-nq", dest="kershaw_nq", type=int, default=9)
+    ap.add_argument("--kershaw-minres-rtol", dest="kershaw_minres_rtol", type=float, default=1e-12)
     ap.add_argument("--sweep-sizes", dest="sweep_sizes", type=int, nargs="+",
                     default=[4, 8, 16, 24, 32, 48])
     ap.add_argument("--sweep-precisions", dest="sweep_precisions", nargs="+", default=["fp64", "fp32"])
@@ -541,7 +587,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.workload != "newton":
         out = {"batched": run_batched, "serving": run_serving, "sweep": run_sweep,
-               "solve": run_solve}[args.workload](args)
+               "solve": run_solve, "kershaw": run_kershaw}[args.workload](args)
         if rank == 0:
             print(json.dumps(out))
         return

@@ -24,7 +24,9 @@ for p in (1, 2, 3, 4):
         CASES.append((2, p, p + dq, 2, 0))
         CASES.append((3, p, p + dq, 303 if p % 2 else 302, 0))
 CASES += [(2, 2, 3, 55, 0), (3, 2, 3, 55, 0), (3, 3, 4, 30355, 1), (3, 1, 2, 30355, 1),
-          (3, 4, 5, 30355, 1), (2, 3, 4, 55, 1), (3, 2, 3, 302, 1)]
+          (3, 4, 5, 30355, 1), (2, 3, 4, 55, 1), (3, 2, 3, 302, 1),
+          # the 9^3-point rule of the paper's Kershaw runs
+          (3, 1, 9, 303, 0), (3, 2, 9, 302, 0), (3, 4, 9, 303, 0)]
 
 
 def _ids(c):
@@ -32,7 +34,7 @@ def _ids(c):
 
 
 NATIVE_CASES = [(2, 2, 3, 2, 0), (2, 4, 6, 2, 0), (3, 1, 2, 302, 0), (3, 3, 4, 303, 0),
-                (3, 4, 5, 302, 0), (3, 2, 3, 30355, 1)]
+                (3, 4, 5, 302, 0), (3, 2, 3, 30355, 1), (3, 3, 9, 303, 0)]
 PARAMS = [(c, "fp64") for c in CASES] + [(c, "fp64-native") for c in NATIVE_CASES]
 
 
@@ -220,4 +222,20 @@ def test_cfg1_solve_reaches_uniform_mesh():
             assert abs(rg["grad_norm"] - ro["grad_norm"]) <= 1e-12 * ro["grad_norm"]
     assert np.abs(xo - ideal).max() <= 1e-10 * m.h
     assert np.abs(host(xg) - ideal).max() <= 1e-10 * m.h
+    gm.close()
+
+
+@pytest.mark.parametrize("p,nq,prec", [(1, 9, "fp64"), (2, 9, "fp64"), (3, 5, "fp64"), (2, 9, "fp32")])
+def test_kershaw_solve_reaches_uniform_mesh(p, nq, prec):
+    """The Kershaw mesh (sliding boundary) solved on the GPU ends at the
+    uniform mesh, as the paper states and the oracle confirms."""
+    from paper_2205_12721_b300 import meshgen as mg
+    m = mg.kershaw(p, (6, 2, 2), 0.3, 0.3)
+    u = mg.structured(3, p, (6, 2, 2))
+    gm = gpu_mesh(m, 303, nq, precision=prec)
+    x = dev(m.x)
+    reps = gm.solve(x, max_newton=40, rtol=1e-11, minres_rtol=1e-10, minres_max_it=200)
+    assert all(r["status"] == 0 for r in reps)
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert np.abs(host(x) - u.x).max() < tol / 6
     gm.close()
