@@ -41,6 +41,7 @@ class _Mesh(ctypes.Structure):
         ("num_elems", ctypes.c_int64), ("num_nodes", ctypes.c_int64),
         ("metric", ctypes.c_int), ("target", ctypes.c_int), ("target_h0", ctypes.c_double),
         ("map", ctypes.c_void_p), ("fixed", ctypes.c_void_p),
+        ("limit_delta", ctypes.c_double), ("x0", ctypes.c_void_p),
     ]
 
 
@@ -136,13 +137,18 @@ class Mesh:
     fixed: np.ndarray | None = None   # (dim*Nx,) uint8
     target: int = TARGET_IDENTITY
     target_h0: float = 1.0
+    limit_delta: float = 0.0           # > 0 with x0: limiting term |x - x0|^2 / delta^2
+    x0: np.ndarray | None = None
 
     def __post_init__(self):
         self.map = np.ascontiguousarray(self.map, dtype=np.int32)
         if self.fixed is not None:
             self.fixed = np.ascontiguousarray(self.fixed, dtype=np.uint8)
+        if self.x0 is not None:
+            self.x0 = np.ascontiguousarray(self.x0, dtype=np.float64)
         self._c = _Mesh(self.dim, self.order, self.nq1d, self.map.shape[0], self.num_nodes,
-                        self.metric, self.target, self.target_h0, _p(self.map), _p(self.fixed))
+                        self.metric, self.target, self.target_h0, _p(self.map), _p(self.fixed),
+                        self.limit_delta, _p(self.x0))
 
     @property
     def ndof(self):

@@ -335,6 +335,8 @@ typedef struct {
     double target_h0;          /* W = h0 * s(x)^(1/d) I for the size target */
     const int32_t *map;        /* num_elems x (order+1)^dim, lexicographic */
     const uint8_t *fixed;      /* dim*num_nodes, or NULL */
+    double limit_delta;        /* > 0: limiting term xi = |x - x0|^2 / delta^2 (Sec. 3.5) */
+    const double *x0;          /* reference positions of the limiting term */
 } or_mesh;
 
 typedef struct {
@@ -425,6 +427,18 @@ static void jacobian(const or_tables *t, const double *xe, int q, double *A)
         }
 }
 
+/* value of the element field u (d components) at point q: sum_i u_i w_i(chi_q) */
+static void interp(const or_tables *t, const double *ue, int q, double *out)
+{
+    for (int a = 0; a < t->d; ++a) {
+        double s = 0;
+        for (int i = 0; i < t->np; ++i) s += ue[a * t->np + i] * t->phi[q * t->np + i];
+        out[a] = s;
+    }
+}
+
+static int limiting_on(const or_mesh *M) { return M->limit_delta > 0 && M->x0 != NULL; }
+
 static void matmul(int d, const double *X, const double *Y, double *Z)
 {
     for (int i = 0; i < d; ++i)
@@ -454,12 +468,14 @@ int or_energy(const or_mesh *M, const double *x, const double *xw, const int64_t
     if (!elems) n_elems = M->num_elems;
     int d = t.d;
     double *xe = malloc(sizeof(double) * d * t.np), *xwe = malloc(sizeof(double) * d * t.np);
+    double *x0e = malloc(sizeof(double) * d * t.np);
     double F = 0, S = 0, mind = INFINITY;
     int inverted = 0;
     for (int64_t k = 0; k < n_elems; ++k) {
         int64_t e = elem_at(elems, k);
         gather_elem(M, &t, x, e, xe);
         gather_elem(M, &t, xw, e, xwe);
+        if (limiting_on(M)) gather_elem(M, &t, M->x0, e, x0e);
         for (int q = 0; q < t.nqd; ++q) {
             double A[9], Winv[9], T[9], mu;
             jacobian(&t, xe, q, A);
@@ -472,9 +488,16 @@ int or_energy(const or_mesh *M, const double *x, const double *xw, const int64_t
             if (!(detA > 0)) { inverted = 1; continue; }
             or_metric(M->metric, d, T, &mu, NULL, NULL);
             F += c * mu;
+            if (limiting_on(M)) {          /* + integral of |x - x0|^2 / delta^2 (eq. F_full) */
+                double xq[3], x0q[3], r2 = 0;
+                interp(&t, xe, q, xq);
+                interp(&t, x0e, q, x0q);
+                for (int a = 0; a < d; ++a) r2 += (xq[a] - x0q[a]) * (xq[a] - x0q[a]);
+                F += c * r2 / (M->limit_delta * M->limit_delta);
+            }
         }
     }
-    free(xe); free(xwe); tables_free(&t);
+    free(xe); free(xwe); free(x0e); tables_free(&t);
     if (min_det_out) *min_det_out = mind;
     if (scale_out) *scale_out = S;
     if (inverted) { *F_out = INFINITY; return OR_ERR_INVERTED; }
@@ -522,17 +545,32 @@ int or_gradient(const or_mesh *M, const double *x, const double *xw, const int64
     memset(g, 0, sizeof(double) * ndof);
     if (absg) memset(absg, 0, sizeof(double) * ndof);
     double *xe = malloc(sizeof(double) * d * t.np), *xwe = malloc(sizeof(double) * d * t.np);
+    double *x0e = malloc(sizeof(double) * d * t.np);
     int rc = OR_OK;
     if (!xw) xw = x;
     for (int64_t k = 0; k < n_elems; ++k) {
         int64_t e = elem_at(elems, k);
         gather_elem(M, &t, x, e, xe);
         gather_elem(M, &t, xw, e, xwe);
+        if (limiting_on(M)) gather_elem(M, &t, M->x0, e, x0e);
         for (int q = 0; q < t.nqd; ++q) {
             double A[9], Winv[9], T[9], P[9], mu;
             jacobian(&t, xe, q, A);
             double detW = target_at(M, &t, xwe, q, Winv);
             matmul(d, A, Winv, T);
+            if (limiting_on(M)) {          /* d/dx_{a,i}: c 2 (x - x0)_a w_i / delta^2 */
+                double xq[3], x0q[3], c2 = t.w[q] * detW * 2.0 / (M->limit_delta * M->limit_delta);
+                interp(&t, xe, q, xq);
+                interp(&t, x0e, q, x0q);
+                for (int i = 0; i < t.np; ++i) {
+                    int64_t node = M->map[e * t.np + i];
+                    for (int a = 0; a < d; ++a) {
+                        double term = c2 * (xq[a] - x0q[a]) * t.phi[q * t.np + i];
+                        g[a * M->num_nodes + node] += term;
+                        if (absg) absg[a * M->num_nodes + node] += fabs(term);
+                    }
+                }
+            }
             if (or_metric(M->metric, d, T, &mu, P, NULL) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
             double c = t.w[q] * detW, PA[9];
             for (int a = 0; a < d; ++a)
@@ -558,7 +596,7 @@ int or_gradient(const or_mesh *M, const double *x, const double *xw, const int64
     if (M->fixed)
         for (int64_t j = 0; j < ndof; ++j)
             if (M->fixed[j]) { g[j] = 0; if (absg) absg[j] = 0; }
-    free(xe); free(xwe); tables_free(&t);
+    free(xe); free(xwe); free(x0e); tables_free(&t);
     return rc;
 }
 
@@ -617,6 +655,20 @@ static int hessian_apply_impl(const or_mesh *M, const double *x, const double *v
                 ve[a * t.np + i] = (M->fixed && M->fixed[j]) ? 0.0 : v[j];
             }
         for (int q = 0; q < t.nqd; ++q) {
+            if (limiting_on(M)) {          /* eq. pa_limiting: c 2/delta^2 w_i sum_j v_{a,j} w_j */
+                double Winv[9], vq[3];
+                double c2 = t.w[q] * target_at(M, &t, xe, q, Winv) * 2.0 /
+                            (M->limit_delta * M->limit_delta);
+                interp(&t, ve, q, vq);
+                for (int i = 0; i < t.np; ++i) {
+                    int64_t node = M->map[e * t.np + i];
+                    for (int a = 0; a < d; ++a) {
+                        double term = c2 * vq[a] * t.phi[q * t.np + i];
+                        y[a * M->num_nodes + node] += term;
+                        if (absy) absy[a * M->num_nodes + node] += fabs(term);
+                    }
+                }
+            }
             double HAl[81];
             const double *HA = HAl;
             if (HAcache) HA = HAcache + ((int64_t)e * t.nqd + q) * dd * dd;
@@ -704,6 +756,16 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
         int64_t e = elem_at(elems, k);
         gather_elem(M, &t, x, e, xe);
         for (int q = 0; q < t.nqd; ++q) {
+            if (limiting_on(M)) {          /* c 2/delta^2 w_i^2 */
+                double Winv[9];
+                double c2 = t.w[q] * target_at(M, &t, xe, q, Winv) * 2.0 /
+                            (M->limit_delta * M->limit_delta);
+                for (int i = 0; i < t.np; ++i) {
+                    int64_t node = M->map[e * t.np + i];
+                    double ph = t.phi[q * t.np + i];
+                    for (int a = 0; a < d; ++a) diag[a * M->num_nodes + node] += c2 * ph * ph;
+                }
+            }
             double HA[81];
             if (hess_A(M, &t, xe, q, HA) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
             for (int i = 0; i < t.np; ++i) {
