@@ -93,6 +93,8 @@ typedef struct {
     int target;          /* TMOP_TARGET_* */
     double target_h0;    /* h0 of the size target (ignored for IDENTITY) */
     int hess_precision;  /* TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE */
+    double limit_delta;  /* > 0: add the limiting term |x - x0|^2 / delta^2 (Sec. 3.5,
+                            eq. F_full); x0 is given by tmop_set_limit_reference.  0: off */
 } tmop_desc;
 
 typedef struct {
@@ -277,6 +279,13 @@ int64_t tmop_batch_device_bytes(const tmop_batch *b);
 
 /* Free the batch and all its meshes.  NULL is accepted. */
 void tmop_batch_destroy(tmop_batch *b);
+
+/* Reference positions x0 of the limiting term xi = |x - x0|^2 / delta^2
+ * (paper Sec. 3.5; its Hessian is the mass-like operator of eq.
+ * pa_limiting).  x0: device FP64, dim * num_nodes; copied.  Required before
+ * any evaluation of a context created with limit_delta > 0; TMOP_ERR_ARG
+ * for a context without the term.  Asynchronous. */
+tmop_status tmop_set_limit_reference(tmop_ctx *ctx, const double *x0);
 
 /* Free the context and everything it owns.  NULL is accepted. */
 void tmop_destroy(tmop_ctx *ctx);

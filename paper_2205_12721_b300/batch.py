@@ -21,13 +21,15 @@ class TmopBatch:
                  minres_fixed_its=False, ls_factor=1.2, ls_max_halvings=20, newton_rtol=1e-10,
                  newton_max_it=100, stream=None):
         self.dim, self.order = dim, order
-        self.stream = stream
+        # each batch works on its own stream unless told otherwise, so that
+        # batches stepped from different host threads overlap on the GPU
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         opts = capi.SolverOpts(minres_rtol, minres_max_it, int(minres_fixed_its), ls_factor,
                                ls_max_halvings)
         self.desc = capi.BatchDesc(dim, order, nq1d or order + 1, metric, target,
                                    PRECISIONS[precision], max_meshes, opts, newton_rtol,
                                    newton_max_it)
-        self.handle = capi.tmop_batch_create(self.desc, stream)
+        self.handle = capi.tmop_batch_create(self.desc, self.stream)
         self.ndof = {}
 
     def close(self):
@@ -42,10 +44,12 @@ class TmopBatch:
             pass
 
     def add(self, emap, num_nodes, x, fixed=None, h0=1.0) -> int:
-        emap_d = torch.from_numpy(np.ascontiguousarray(emap, dtype=np.int32)).cuda()
-        fixed_d = None if fixed is None else torch.from_numpy(
-            np.ascontiguousarray(fixed, dtype=np.uint8)).cuda()
-        x_d = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        with torch.cuda.stream(self.stream):
+            emap_d = torch.from_numpy(np.ascontiguousarray(emap, dtype=np.int32)).cuda()
+            fixed_d = None if fixed is None else torch.from_numpy(
+                np.ascontiguousarray(fixed, dtype=np.uint8)).cuda()
+            x_d = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        self.stream.synchronize()
         slot = capi.tmop_batch_add(self.handle, int(emap.shape[0]), int(num_nodes), emap_d, fixed_d,
                                    x_d, h0)
         self.ndof[slot] = self.dim * int(num_nodes)
@@ -67,9 +71,10 @@ class TmopBatch:
         return capi.tmop_batch_state(self.handle, slot)
 
     def positions(self, slot) -> torch.Tensor:
-        x = torch.empty(self.ndof[slot], dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(self.stream):
+            x = torch.empty(self.ndof[slot], dtype=torch.float64, device="cuda")
         capi.tmop_batch_positions(self.handle, slot, x)
-        torch.cuda.synchronize()
+        self.stream.synchronize()
         return x
 
     def remove(self, slot):
@@ -84,3 +89,12 @@ class TmopBatch:
             if self.step() == 0:
                 break
         return n
+
+
+def step_all(batches, pool=None):
+    """One Newton step of every batch; with a thread pool the batches run
+    from different host threads on their own streams and overlap on the GPU
+    (the library calls release the GIL).  Returns the active counts."""
+    if pool is None or len(batches) < 2:
+        return [b.step() for b in batches]
+    return list(pool.map(lambda b: b.step(), batches))

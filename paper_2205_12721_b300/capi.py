@@ -28,7 +28,7 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc",
            "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
            "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
-           "tmop_batch_device_bytes", "tmop_batch_destroy")
+           "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference")
 
 
 class TmopError(RuntimeError):
@@ -41,7 +41,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("nq1d", ctypes.c_int),
                 ("num_elems", ctypes.c_int64), ("num_nodes", ctypes.c_int64),
                 ("metric", ctypes.c_int), ("target", ctypes.c_int),
-                ("target_h0", ctypes.c_double), ("hess_precision", ctypes.c_int)]
+                ("target_h0", ctypes.c_double), ("hess_precision", ctypes.c_int),
+                ("limit_delta", ctypes.c_double)]
 
 
 class SolverOpts(ctypes.Structure):
@@ -117,6 +118,7 @@ def lib():
             "tmop_batch_mesh_bytes": (I64, [P, I64, I64]),
             "tmop_batch_device_bytes": (I64, [P]),
             "tmop_batch_destroy": (None, [P]),
+            "tmop_set_limit_reference": (I, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -197,6 +199,10 @@ def tmop_newton_step(ctx: int, x, opts: SolverOpts | None = None) -> dict:
     d = rep.as_dict()
     d["status"] = st
     return d
+
+
+def tmop_set_limit_reference(ctx: int, x0):
+    _check(lib().tmop_set_limit_reference(ctx, _ptr(x0)), "tmop_set_limit_reference")
 
 
 def tmop_destroy(ctx: int):

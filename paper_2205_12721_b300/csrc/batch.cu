@@ -612,6 +612,7 @@ tmop_status setup_and_minres(tmop_batch *b)
 {
     const tmop_batch_desc &D = b->desc;
     ElemParams P0{};
+    P0.metric = b->desc.metric;            // selects the set-up kernel family
     BatchArgs a = bargs(b, ROLE_X, -1, ROLE_H, false);
     BCK(launch_hsetup(b->d, b->p, b->nq, P0, nullptr, nullptr, b->desc.hess_precision, b->stream, &a,
                       b->nt_e));

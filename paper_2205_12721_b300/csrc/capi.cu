@@ -86,6 +86,10 @@ struct tmop_ctx {
     void *kv[8] = {nullptr};     // v, R1, R2, Z, W1, W2, W3, spare
     MinresState *st = nullptr, *hst = nullptr;
     int check_every = 4;
+    // limiting term
+    double lim2 = 0.0;                 // 2 / delta^2, 0 when off
+    double *x0 = nullptr, *lim_cq = nullptr, *part2 = nullptr;
+    bool x0_set = false;
     // instrumentation
     bool prof = false;
     std::vector<ProfRec> pending;
@@ -191,14 +195,34 @@ bool metric_ok(int m, int d)
     return m == TMOP_METRIC_55;
 }
 
+tmop_status limit_ready(tmop_ctx *c)
+{
+    if (c->lim2 > 0.0 && !c->x0_set)
+        return fail(TMOP_ERR_ARG, "limit_delta > 0 but tmop_set_limit_reference has not been called");
+    return TMOP_OK;
+}
+
+// Limiting energy into scal[4] (and its gradient added into ev64 when ev).
+tmop_status limit_eg_async(tmop_ctx *c, const double *x, double *ev)
+{
+    if (c->lim2 <= 0.0) return TMOP_OK;
+    const ElemParams P = c->params();
+    const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
+    CK(launch_limit_eg(c->d, c->p, c->nq, P, x, c->x0, c->lim2, c->part2, ev, c->arith, c->stream));
+    CK(launch_finalize_energy(c->part2, nb, c->scal + 4, c->stream));
+    return TMOP_OK;
+}
+
 // Energy + min det into ctx->scal[0..1] (device), no sync.
 tmop_status energy_async(tmop_ctx *c, const double *x)
 {
+    TRY(limit_ready(c));
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
     TRY(timed(c, TMOP_K_ENERGY, "energy kernel",
               [&] { return launch_energy(c->d, c->p, c->nq, P, x, c->part, c->arith, c->stream); }));
     CK(launch_finalize_energy(c->part, nb, c->scal, c->stream));
+    TRY(limit_eg_async(c, x, nullptr));
     return TMOP_OK;
 }
 
@@ -212,21 +236,23 @@ tmop_status read_scalars(tmop_ctx *c, int n)
 tmop_status energy_sync(tmop_ctx *c, const double *x, double *F, double *md)
 {
     TRY(energy_async(c, x));
-    TRY(read_scalars(c, 2));
+    TRY(read_scalars(c, 6));
     *md = c->hscal[1];
     if (!(c->hscal[1] > 0.0) && c->E > 0) {
         *F = INFINITY;
         return fail(TMOP_ERR_INVERTED, "det(A) <= 0 at some quadrature point");
     }
-    *F = c->hscal[0];
+    *F = c->hscal[0] + (c->lim2 > 0.0 ? c->hscal[4] : 0.0);
     return TMOP_OK;
 }
 
 tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
 {
+    TRY(limit_ready(c));
     const ElemParams P = c->params();
     TRY(timed(c, TMOP_K_GRADIENT, "gradient kernel",
               [&] { return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->arith, c->stream); }));
+    TRY(limit_eg_async(c, x, c->ev64));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 0,
                                c->Nx, c->d, c->ENP, g, TMOP_FP64, nullptr, 0, c->stream);
@@ -238,6 +264,7 @@ tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
 // F and min det on the host (synchronises).
 tmop_status energy_grad_sync(tmop_ctx *c, const double *x, double *g, double *F, double *md)
 {
+    TRY(limit_ready(c));
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
     TRY(timed(c, TMOP_K_GRADIENT, "energy+gradient kernel", [&] {
@@ -245,17 +272,18 @@ tmop_status energy_grad_sync(tmop_ctx *c, const double *x, double *g, double *F,
                                c->part);
     }));
     CK(launch_finalize_energy(c->part, nb, c->scal, c->stream));
+    TRY(limit_eg_async(c, x, c->ev64));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 0,
                                c->Nx, c->d, c->ENP, g, TMOP_FP64, nullptr, 0, c->stream);
     }));
-    TRY(read_scalars(c, 2));
+    TRY(read_scalars(c, 6));
     *md = c->hscal[1];
     if (!(c->hscal[1] > 0.0) && c->E > 0) {
         *F = INFINITY;
         return fail(TMOP_ERR_INVERTED, "det(A) <= 0 at some quadrature point");
     }
-    *F = c->hscal[0];
+    *F = c->hscal[0] + (c->lim2 > 0.0 ? c->hscal[4] : 0.0);
     return TMOP_OK;
 }
 
@@ -273,9 +301,11 @@ tmop_status norm_sync(tmop_ctx *c, const double *a, double *out)
 
 tmop_status hsetup_async(tmop_ctx *c, const double *x)
 {
+    TRY(limit_ready(c));
     const ElemParams P = c->params();
     TRY(timed(c, TMOP_K_HSETUP, "hessian setup kernel",
               [&] { return launch_hsetup(c->d, c->p, c->nq, P, x, c->H, c->prec, c->stream); }));
+    if (c->lim2 > 0.0) CK(launch_limit_setup(c->d, c->p, c->nq, P, x, c->lim2, c->lim_cq, c->stream));
     c->h_ready = true;
     return TMOP_OK;
 }
@@ -287,6 +317,8 @@ tmop_status apply_internal(tmop_ctx *c, const void *v, void *y, const int *stop,
     TRY(timed(c, TMOP_K_APPLY, "apply kernel", [&] {
         return launch_apply(c->d, c->p, c->nq, P, v, c->H, c->evR, c->prec, stop, k, c->stream);
     }));
+    if (c->lim2 > 0.0)
+        CK(launch_limit_apply(c->d, c->p, c->nq, P, v, c->lim_cq, c->evR, c->prec, stop, k, c->stream));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
                                c->Nx, c->d, c->ENP, y, c->vprec, stop, k, c->stream);
@@ -300,6 +332,7 @@ tmop_status diag_async(tmop_ctx *c, void *diag)
     TRY(timed(c, TMOP_K_DIAG, "diag kernel", [&] {
         return launch_diag(c->d, c->p, c->nq, P, c->H, c->evR, c->prec, c->stream);
     }));
+    if (c->lim2 > 0.0) CK(launch_limit_diag(c->d, c->p, c->nq, P, c->lim_cq, c->evR, c->prec, c->stream));
     TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 2,
                                c->Nx, c->d, c->ENP, diag, c->vprec, nullptr, 0, c->stream);
@@ -411,6 +444,8 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
         return fail(TMOP_ERR_ARG, "unknown target");
     if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
         return fail(TMOP_ERR_ARG, "target_h0 must be > 0");
+    if (D.limit_delta < 0.0 || D.limit_delta != D.limit_delta)
+        return fail(TMOP_ERR_ARG, "limit_delta must be >= 0");
     if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32 &&
         D.hess_precision != TMOP_FP64_NATIVE)
         return fail(TMOP_ERR_ARG, "hess_precision must be TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE");
@@ -526,6 +561,12 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     STRY(c->alloc_raw(&c->diagR, c->rsz * ndof));
     STRY(c->alloc_raw(&c->minv, c->rsz * ndof));
     for (int i = 0; i < 8; ++i) STRY(c->alloc_raw(&c->kv[i], c->rsz * ndof));
+    if (D.limit_delta > 0.0) {
+        c->lim2 = 2.0 / (D.limit_delta * D.limit_delta);
+        STRY(c->alloc(&c->x0, ndof));
+        STRY(c->alloc(&c->lim_cq, (size_t)c->E * c->nqd));
+        STRY(c->alloc(&c->part2, c->part_n));
+    }
     SCK(cudaMallocHost((void **)&c->hscal, 8 * sizeof(double)));
     SCK(cudaMallocHost((void **)&c->hst, sizeof(MinresState)));
     SCK(cudaStreamSynchronize(c->stream));
@@ -567,6 +608,9 @@ tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y)
         return launch_apply(ctx->d, ctx->p, ctx->nq, P, ctx->vm, ctx->H, ctx->evR, ctx->prec,
                             nullptr, 0, ctx->stream);
     }));
+    if (ctx->lim2 > 0.0)
+        CK(launch_limit_apply(ctx->d, ctx->p, ctx->nq, P, ctx->vm, ctx->lim_cq, ctx->evR, ctx->prec,
+                              nullptr, 0, ctx->stream));
     TRY(timed(ctx, TMOP_K_ASSEMBLE, "assemble", [&] {
         return launch_assemble(ctx->evR, ctx->vprec, ctx->csr_ptr, ctx->csr_idx, ctx->fixed, v, 1,
                                ctx->Nx, ctx->d, ctx->ENP, y, ctx->vprec, nullptr, 0, ctx->stream);
@@ -647,6 +691,15 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         return finish(TMOP_OK);
     }
     return finish(fail(TMOP_ERR_LINESEARCH, "no step length passed the line search"));
+}
+
+tmop_status tmop_set_limit_reference(tmop_ctx *ctx, const double *x0)
+{
+    if (!ctx || !x0) return fail(TMOP_ERR_ARG, "NULL argument");
+    if (ctx->lim2 <= 0.0) return fail(TMOP_ERR_ARG, "context has no limiting term (limit_delta = 0)");
+    CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->x0_set = true;
+    return TMOP_OK;
 }
 
 tmop_status tmop_profile_enable(tmop_ctx *ctx, int on)

@@ -4,18 +4,27 @@
 
 namespace tmop {
 
-template <class C, class RS, class RH>
-static cudaError_t run_hsetup(const ElemParams &P, const double *x, RH *H, cudaStream_t s,
-                              const BatchArgs &B, int64_t ntiles)
+template <class C, class RS, class RH, bool I2>
+static cudaError_t run_hsetup_m(const ElemParams &P, const double *x, RH *H, cudaStream_t s,
+                                const BatchArgs &B, int64_t ntiles)
 {
     using L = Layout<C, RS>;
     const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    cudaError_t e = prepare(k_hsetup<C, RS, RH>, L::bytes);
+    cudaError_t e = prepare(k_hsetup<C, RS, RH, I2>, L::bytes);
     if (e != cudaSuccess) return e;
-    k_hsetup<C, RS, RH><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, H, B);
+    k_hsetup<C, RS, RH, I2><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, x, H, B);
     count_launch();
     return cudaGetLastError();
+}
+
+// P.metric selects the kernel family (the batch passes its metric here too)
+template <class C, class RS, class RH>
+static cudaError_t run_hsetup(const ElemParams &P, const double *x, RH *H, cudaStream_t s,
+                              const BatchArgs &B, int64_t ntiles)
+{
+    if (C::D == 3 && P.metric == MET_302) return run_hsetup_m<C, RS, RH, true>(P, x, H, s, B, ntiles);
+    return run_hsetup_m<C, RS, RH, false>(P, x, H, s, B, ntiles);
 }
 
 template <class C>

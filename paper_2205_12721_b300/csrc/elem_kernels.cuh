@@ -245,7 +245,10 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
 }
 
 // ---------------------------------------------------------------- Hessian setup
-template <class C, class RS, class RH>
+// HAS_I2 = false: metrics of (I1, tau) only (mu_2, mu_303, mu_55, mu_303 + mu_55),
+// whose d2mu/dT2 is u (x) g1 + w (x) cof T + 2 f1 Id + f_tau d2tau with
+// u = f11 g1 + f1t cof T, w = f1t g1 + ftt cof T: two FMAs per stored entry.
+template <class C, class RS, class RH, bool HAS_I2>
 __global__ void __launch_bounds__(C::NT)
 k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchArgs BA)
 {
@@ -281,14 +284,37 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         }
         Inv v;
         metric_scalars(P.metric, I1, tau, I2, v);
-        if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
         const double sc = cq * iws * iws;
+        if constexpr (HAS_I2) {
+            if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r)
+            for (int r = 0; r < C::DD; ++r)
 #pragma unroll
-            for (int s = r; s < C::DD; ++s)
-                He[pidx<C::DD>(r, s) * C::NQD + q] =
-                    from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+                for (int s = r; s < C::DD; ++s)
+                    He[pidx<C::DD>(r, s) * C::NQD + q] =
+                        from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+        } else {
+            double u[C::DD], w[C::DD];
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r) {
+                u[r] = sc * (v.f11 * 2.0 * T[r] + v.f1t * Cf[r]);
+                w[r] = sc * (v.f1t * 2.0 * T[r] + v.ftt * Cf[r]);
+            }
+            const double dg = 2.0 * sc * v.f1, ft = sc * v.ft;
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+                for (int s = r; s < C::DD; ++s) {
+                    const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
+                    double k = u[r] * (2.0 * T[s]) + w[r] * Cf[s];
+                    if (r == s) k += dg;
+                    if (a != cc && b != e) {
+                        if (C::D == 2) k += ft * ((a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0));
+                        else k += ft * eps3(a, cc) * eps3(b, e) * T[(3 - a - cc) * 3 + (3 - b - e)];
+                    }
+                    He[pidx<C::DD>(r, s) * C::NQD + q] = from_db<RH>(k);
+                }
+        }
     });
 }
 

@@ -73,6 +73,8 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
     if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
         return set_error(TMOP_ERR_ARG, "target_h0 must be > 0");
     if (D.num_elems < 0 || D.num_nodes <= 0) return set_error(TMOP_ERR_ARG, "bad mesh sizes");
+    if (D.limit_delta != 0.0)
+        return set_error(TMOP_ERR_UNSUPPORTED, "the limiting term is not available without a context");
     if (D.num_elems > 0 && !elem_to_node) return set_error(TMOP_ERR_ARG, "elem_to_node is NULL");
     const int64_t nb = elem_blocks(D.dim, D.order, D.nq1d, D.num_elems);
     if (nb > kMaxCtas)

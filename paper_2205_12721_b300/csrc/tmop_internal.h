@@ -45,6 +45,18 @@ cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v
 cudaError_t launch_diag(int d, int p, int q, const ElemParams &P, const void *H, void *ev, int prec,
                         cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 
+// Limiting term |x - x0|^2 / delta^2 (limit.cu); lim2 = 2 / delta^2.
+cudaError_t launch_limit_eg(int d, int p, int q, const ElemParams &P, const double *x,
+                            const double *x0, double lim2, double *part, double *ev, int arith,
+                            cudaStream_t s);
+cudaError_t launch_limit_setup(int d, int p, int q, const ElemParams &P, const double *x, double lim2,
+                               double *cq, cudaStream_t s);
+cudaError_t launch_limit_apply(int d, int p, int q, const ElemParams &P, const void *v,
+                               const double *cq, void *ev, int prec, const int *stop, int k,
+                               cudaStream_t s);
+cudaError_t launch_limit_diag(int d, int p, int q, const ElemParams &P, const double *cq, void *ev,
+                              int prec, cudaStream_t s);
+
 // Host tables: Gauss-Legendre rule on [0,1], GLL nodes, Lagrange B/G.
 void host_gauss_legendre(int n, double *x, double *w);
 void host_gll_nodes(int n, double *x);

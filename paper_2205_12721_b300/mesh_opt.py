@@ -19,7 +19,7 @@ class TmopMesh:
 
     def __init__(self, dim, order, emap, num_nodes, metric, fixed=None, nq1d=None,
                  target=capi.TARGET_IDENTITY, target_h0=1.0, precision="fp64", device="cuda",
-                 stream=None):
+                 stream=None, limit_delta=0.0, x0=None):
         self.dim, self.order = dim, order
         self.nq1d = nq1d or order + 1
         self.num_nodes = int(num_nodes)
@@ -33,9 +33,17 @@ class TmopMesh:
         self._fixed = None if fixed is None else torch.from_numpy(
             np.ascontiguousarray(fixed, dtype=np.uint8)).to(self.device)
         self.desc = capi.Desc(dim, order, self.nq1d, self.num_elems, self.num_nodes, metric,
-                              target, float(target_h0), self.prec)
+                              target, float(target_h0), self.prec, float(limit_delta))
         self.stream = stream
         self.ctx = capi.tmop_setup(self.desc, self._map, self._fixed, stream)
+        if limit_delta > 0.0 and x0 is not None:
+            self.set_limit_reference(x0)
+
+    def set_limit_reference(self, x0):
+        """Reference positions of the limiting term |x - x0|^2 / delta^2."""
+        x0d = x0 if isinstance(x0, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x0))
+        self._x0 = x0d.to(self.device, torch.float64)
+        capi.tmop_set_limit_reference(self.ctx, self._x0)
 
     @classmethod
     def from_structured(cls, m, metric, **kw):

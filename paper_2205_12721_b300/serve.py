@@ -12,12 +12,13 @@ from __future__ import annotations
 
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import torch
 
 from . import capi, meshgen
-from .batch import TmopBatch
+from .batch import TmopBatch, step_all
 
 
 class Server:
@@ -30,6 +31,7 @@ class Server:
                        max_meshes=max_meshes_per_group, stream=stream)
         self.groups: dict = {}
         self.used = 0
+        self.pool = ThreadPoolExecutor(max_workers=16)
 
     def group(self, dim, order, metric) -> TmopBatch:
         key = (dim, order, metric)
@@ -41,6 +43,7 @@ class Server:
         for g in self.groups.values():
             g.close()
         self.groups.clear()
+        self.pool.shutdown(wait=True)
 
     def run(self, jobs, build=meshgen.serving_mesh, keep_positions=False, clock=time.perf_counter):
         """Serve ``jobs`` (dicts with id, arrival, dim, order, metric, ...).
@@ -72,9 +75,8 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0]["arrival"] - (clock() - t0), 0.01)))
                 continue
-            for key, g in self.groups.items():
-                if any(k == key for k, _ in active):
-                    g.step()
+            live = {k for k, _ in active}
+            step_all([g for key, g in self.groups.items() if key in live], self.pool)
             ticks += 1
             for (key, slot) in list(active):
                 g = self.groups[key]

@@ -169,10 +169,10 @@ def _newton_parity(m, metric, steps, target=0, h0=1.0, nq=None, max_it=200):
         S = O.energy(om, xs)[3]                          # scale sum_q |c_q|
         ro = O.newton_step(om, xs, 1e-8, max_it)
         rg = gm.newton_step(xg, 1e-8, max_it)
-        assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
         g_first = g_first or ro["grad_norm"]
         if ro["grad_norm"] < 1e-8 * g_first:
             break        # converged: F is at rounding level, line-search tests are ties
+        assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
         assert ro["minres_iters"] < max_it, "case must be well conditioned (MINRES converges)"
         assert rg["halvings"] == ro["halvings"], (k, ro, rg)
         assert abs(rg["minres_iters"] - ro["minres_iters"]) <= 1, (k, ro, rg)
@@ -239,3 +239,65 @@ def test_kershaw_solve_reaches_uniform_mesh(p, nq, prec):
     tol = 1e-9 if prec == "fp64" else 1e-5
     assert np.abs(host(x) - u.x).max() < tol / 6
     gm.close()
+
+
+LIMIT_CASES = [((2, 2, 3, 2, 0), "fp64"), ((3, 2, 3, 303, 0), "fp64"), ((3, 3, 4, 302, 0), "fp64"),
+               ((3, 2, 3, 30355, 1), "fp64"), ((3, 2, 3, 303, 0), "fp32"),
+               ((3, 3, 4, 303, 0), "fp64-native"), ((2, 3, 5, 2, 1), "fp64")]
+
+
+@pytest.mark.parametrize("case,precision", LIMIT_CASES, ids=[f"{_ids(c)}-{p}" for c, p in LIMIT_CASES])
+def test_limiting_term_parity(case, precision):
+    """Objective with the limiting term |x - x0|^2 / delta^2 (Sec. 3.5):
+    energy, gradient, Hessian action (shape part + mass-like part) and
+    diagonal against the oracle; one Newton step from the same x."""
+    from paper_2205_12721_b300 import meshgen as mg
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    d, p, nq, metric, target = case
+    shape = SHAPES[d][0]
+    base = mg.structured(d, p, shape)
+    m = mg.perturb_smooth(base, seed=17, amp_smooth=0.05, amp_noise=0.025)
+    h0, delta = 1.0 / max(shape), 0.05
+    om = O.Mesh(d, p, nq, m.map, m.num_nodes, metric, m.fixed, target, h0, delta, base.x)
+    gm = TmopMesh(d, p, m.map, m.num_nodes, metric, fixed=m.fixed, nq1d=nq, target=target,
+                  target_h0=h0, precision=precision, limit_delta=delta, x0=base.x)
+    tol = 2e-6 if precision == "fp32" else TOL
+    x = dev(m.x)
+    st_o, F_o, _, S = O.energy(om, m.x)
+    st, F, _ = gm.energy(x)
+    assert st == 0 and abs(F - F_o) <= TOL * max(abs(F_o), S)
+    g_o, ga = O.gradient(om, m.x, with_abs=True)
+    assert_vec_close(host(gm.gradient(x)), g_o, ga, what="gradient + limiting")
+    gm.hessian_setup(x)
+    v = np.random.default_rng(9).standard_normal(m.ndof)
+    y_o, ya = O.hessian_apply(om, m.x, v, with_abs=True)
+    rd = torch.float32 if precision == "fp32" else torch.float64
+    assert_vec_close(host(gm.hessian_apply(dev(v, rd))), y_o, ya, tol=tol, what="apply + limiting")
+    dg_o = O.hessian_diag(om, m.x)
+    assert_vec_close(host(gm.hessian_diag()), dg_o, np.abs(dg_o), tol=tol, what="diag + limiting")
+    if precision != "fp32":
+        # a fixed number of MINRES iterations on both sides (no stop-test tie)
+        xo = m.x.copy()
+        ro = O.newton_step(om, xo, 0.0, 30, minres_fixed_its=True)
+        rg = gm.newton_step(x, 0.0, 30, minres_fixed_its=True)
+        assert ro["status"] == 0 and rg["status"] == 0
+        assert np.abs(host(x) - xo).max() <= 1e-10 * m.h
+    gm.close()
+
+
+def test_limiting_requires_reference():
+    from paper_2205_12721_b300 import meshgen as mg
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    m = mg.structured(2, 2, 3)
+    gm = TmopMesh(2, 2, m.map, m.num_nodes, 2, fixed=m.fixed, limit_delta=0.1)
+    with pytest.raises(capi.TmopError) as ei:
+        gm.gradient(dev(m.x))
+    assert ei.value.status == capi.ERR_ARG
+    gm.set_limit_reference(m.x)
+    g = host(gm.gradient(dev(m.x)))
+    assert np.abs(g).max() < 1e-12            # ideal mesh at its own reference
+    gm.close()
+    plain = TmopMesh(2, 2, m.map, m.num_nodes, 2, fixed=m.fixed)
+    with pytest.raises(capi.TmopError):
+        plain.set_limit_reference(m.x)
+    plain.close()
