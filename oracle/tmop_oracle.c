@@ -237,16 +237,24 @@ static void i2_derivs(const double *T, double I1, double *I2, double *dI2, doubl
                 }
 }
 
-/* mu, P = dmu/dT, K = d2mu/dT2 for metric id 2 (2D), 302, 303 (3D), 55 (any d)
- * and 30355 = mu_303 + mu_55 (3D).  P or K may be NULL.  Returns OR_ERR_ARG
- * for an unknown (metric, d) pair and OR_ERR_INVERTED when det T <= 0. */
+/* mu, P = dmu/dT, K = d2mu/dT2 for metric id 2 (2D), 302, 303 (3D), 55 (any d),
+ * 30355 = mu_303 + mu_55 (3D), and the shape+size metrics of Sec. 2.2
+ * 7: mu = |T - T^-t|^2 and 9: mu = tau |T - T^-t|^2 (any d).  P or K may be
+ * NULL.  Returns OR_ERR_ARG for an unknown (metric, d) pair and
+ * OR_ERR_INVERTED when det T <= 0.
+ *
+ * mu_7 and mu_9 through the invariants: <T, T^-t> = tr(T^-1 T) = d, so
+ * |T - T^-t|^2 = I1 - 2d + |T^-1|^2, with |T^-1|^2 = I2 / tau^2 in 3D and
+ * I1 / tau^2 in 2D (the 2D cofactor is a signed permutation of T).  mu itself
+ * is evaluated from the definition with the explicit inverse. */
 int or_metric(int id, int d, const double *T, double *mu, double *P, double *K)
 {
     int dd = d * d;
     double I1 = 0;
     for (int i = 0; i < dd; ++i) I1 += T[i] * T[i];
     double tau = det_def(d, T);
-    int ok = (id == 2 && d == 2) || ((id == 302 || id == 303 || id == 30355) && d == 3) || id == 55;
+    int ok = (id == 2 && d == 2) || ((id == 302 || id == 303 || id == 30355) && d == 3) ||
+             id == 55 || id == 7 || id == 9;
     if (!ok) return OR_ERR_ARG;
     if (!(tau > 0)) return OR_ERR_INVERTED;
 
@@ -283,6 +291,31 @@ int or_metric(int id, int d, const double *T, double *mu, double *P, double *K)
         m = I1 * J / 9.0 - 1.0;
         use_I2 = 1;
     }
+    if (id == 7 || id == 9) {
+        double Ti[9], n2 = 0;
+        inv_def(d, T, Ti);
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                double r = T[a * d + b] - Ti[b * d + a];
+                n2 += r * r;
+            }
+        m = (id == 7) ? n2 : tau * n2;
+        if (d == 3) {
+            use_I2 = 1;
+        } else if (id == 7) {                /* I1 + I1/tau^2 - 4 */
+            double t2 = tau * tau;
+            f[0] = 1.0 + 1.0 / t2;
+            f[1] = -2.0 * I1 / (t2 * tau);
+            ff[0][1] = ff[1][0] = -2.0 / (t2 * tau);
+            ff[1][1] = 6.0 * I1 / (t2 * t2);
+        } else {                             /* tau I1 + I1/tau - 4 tau */
+            double t2 = tau * tau;
+            f[0] = tau + 1.0 / tau;
+            f[1] = I1 - I1 / t2 - 4.0;
+            ff[0][1] = ff[1][0] = 1.0 - 1.0 / t2;
+            ff[1][1] = 2.0 * I1 / (t2 * tau);
+        }
+    }
     if (mu) *mu = m;
     if (!P && !K) return OR_OK;
 
@@ -296,13 +329,28 @@ int or_metric(int id, int d, const double *T, double *mu, double *P, double *K)
         double I2;
         i2_derivs(T, I1, &I2, dU[2], d2U[2]);
         double t2 = tau * tau;
-        f[0] = I2 / (9.0 * t2);
-        f[2] = I1 / (9.0 * t2);
-        f[1] = -2.0 * I1 * I2 / (9.0 * t2 * tau);
-        ff[0][2] = ff[2][0] = 1.0 / (9.0 * t2);
-        ff[0][1] = ff[1][0] = -2.0 * I2 / (9.0 * t2 * tau);
-        ff[2][1] = ff[1][2] = -2.0 * I1 / (9.0 * t2 * tau);
-        ff[1][1] = 2.0 * I1 * I2 / (3.0 * t2 * t2);
+        if (id == 7) {                       /* I1 + I2/tau^2 - 6 */
+            f[0] = 1.0;
+            f[2] = 1.0 / t2;
+            f[1] = -2.0 * I2 / (t2 * tau);
+            ff[2][1] = ff[1][2] = -2.0 / (t2 * tau);
+            ff[1][1] = 6.0 * I2 / (t2 * t2);
+        } else if (id == 9) {                /* tau I1 + I2/tau - 6 tau */
+            f[0] = tau;
+            f[2] = 1.0 / tau;
+            f[1] = I1 - I2 / t2 - 6.0;
+            ff[0][1] = ff[1][0] = 1.0;
+            ff[2][1] = ff[1][2] = -1.0 / t2;
+            ff[1][1] = 2.0 * I2 / (t2 * tau);
+        } else {                             /* 302: I1 I2 / (9 tau^2) - 1 */
+            f[0] = I2 / (9.0 * t2);
+            f[2] = I1 / (9.0 * t2);
+            f[1] = -2.0 * I1 * I2 / (9.0 * t2 * tau);
+            ff[0][2] = ff[2][0] = 1.0 / (9.0 * t2);
+            ff[0][1] = ff[1][0] = -2.0 * I2 / (9.0 * t2 * tau);
+            ff[2][1] = ff[1][2] = -2.0 * I1 / (9.0 * t2 * tau);
+            ff[1][1] = 2.0 * I1 * I2 / (3.0 * t2 * t2);
+        }
     }
     int nu = use_I2 ? 3 : 2;
     if (P)

@@ -45,7 +45,8 @@ def test_ideal_mesh_zero_energy_and_gradient(oracle_mod, d, p, metric):
         assert np.abs(g2).max() < 1e-12
 
 
-@pytest.mark.parametrize("d,metric", [(2, 2), (3, 302), (3, 303), (3, 55), (2, 55)])
+@pytest.mark.parametrize("d,metric", [(2, 2), (3, 302), (3, 303), (3, 55), (2, 55),
+                                      (2, 7), (3, 7), (2, 9), (3, 9)])
 def test_affine_element_energy_is_mu(oracle_mod, d, metric):
     rng = np.random.default_rng(3)
     for order in (1, 2, 3):
@@ -94,6 +95,36 @@ def test_size_target_energy_matches_integral(oracle_mod):
             assert abs(F3 - ref) < 1e-9 * ref
 
 
+@pytest.mark.parametrize("metric", [7, 9])
+def test_shape_size_metric_size_target_integral(oracle_mod, metric):
+    """Ideal mesh, W = h s^(1/d) I: T = t I with t = s^(-1/d), c_q = w_q h^d s,
+    mu_7 = d (t - 1/t)^2 and mu_9 = t^d mu_7, so F = integral of
+    s d (t - 1/t)^2 (mu_7) or d (t - 1/t)^2 (mu_9) over the unit cube."""
+    for d in (2, 3):
+        n = 6 if d == 2 else 4
+        m = mg.structured(d, 2, n)
+        M = _om(oracle_mod, m, metric, nq=10, target=1, h0=1.0 / n)
+        st, F, _, _ = oracle_mod.energy(M, m.x)
+
+        def f(*xs):
+            s = 0.5
+            for t in xs:
+                s = s * np.sin(2 * np.pi * t)
+            s = 1 + s
+            t = s ** (-1.0 / d)
+            v = d * (t - 1 / t) ** 2
+            return s * v if metric == 7 else v
+        t, w = np.polynomial.legendre.leggauss(60)
+        t = (t + 1) / 2; w = w / 2
+        G = np.meshgrid(*([t] * d), indexing="ij")
+        W = np.ones_like(G[0])
+        for k in range(d):
+            W = W * w.reshape([-1 if j == k else 1 for j in range(d)])
+        ref = float(np.sum(W * f(*G)))
+        assert st == 0
+        assert abs(F - ref) < 1e-9 * ref
+
+
 @pytest.mark.parametrize("d,p,metric", [(2, 2, 2), (3, 2, 302), (3, 3, 303)])
 def test_rotation_scale_equivariance(oracle_mod, d, p, metric):
     n = 3 if d == 3 else 4
@@ -120,7 +151,8 @@ def test_rotation_scale_equivariance(oracle_mod, d, p, metric):
 
 
 @pytest.mark.parametrize("d,p,metric,target", [(2, 2, 2, 0), (2, 3, 2, 0), (3, 1, 302, 0),
-                                               (3, 2, 303, 0), (3, 2, 30355, 1)])
+                                               (3, 2, 303, 0), (3, 2, 30355, 1), (2, 2, 9, 0),
+                                               (3, 2, 7, 1), (3, 1, 9, 1)])
 def test_gradient_and_hessian_vs_finite_differences(oracle_mod, d, p, metric, target):
     n = 3 if d == 3 else 4
     m = mg.perturb_smooth(mg.structured(d, p, n), seed=9, amp_smooth=0.05, amp_noise=0.025)
@@ -144,7 +176,8 @@ def test_gradient_and_hessian_vs_finite_differences(oracle_mod, d, p, metric, ta
         assert np.linalg.norm(fdh[free] - hv[free]) < 1e-6 * np.linalg.norm(hv[free])
 
 
-@pytest.mark.parametrize("d,p,metric", [(2, 2, 2), (3, 2, 302), (3, 2, 303), (3, 1, 30355)])
+@pytest.mark.parametrize("d,p,metric", [(2, 2, 2), (3, 2, 302), (3, 2, 303), (3, 1, 30355),
+                                        (2, 2, 7), (3, 1, 9)])
 def test_dense_hessian_symmetry_and_diagonal(oracle_mod, d, p, metric):
     shape = (2, 1) if d == 2 else (2, 1, 1)
     m = mg.perturb_uniform(mg.structured(d, p, shape), amp=0.1, seed=3)

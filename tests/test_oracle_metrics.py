@@ -1,6 +1,7 @@
 """Pins for the oracle's quality metrics mu(T), dmu/dT, d2mu/dT2
-(paper Sec. 2.2 for mu_2 and mu_55, Sec. 4.1 for mu_303; mu_302 from the
-benchmark configuration |T|^2 |T^-1|^2 / 9 - 1).
+(paper Sec. 2.2 for mu_2, mu_55 and the shape+size metrics
+mu_7 = |T - T^-t|^2, mu_9 = tau |T - T^-t|^2; Sec. 4.1 for mu_303; mu_302 from
+the benchmark configuration |T|^2 |T^-1|^2 / 9 - 1).
 
 mu is checked against hand values; P against complex-step derivatives of the
 definition; K against exact symbolic second derivatives (sympy)."""
@@ -8,7 +9,8 @@ import numpy as np
 import pytest
 import sympy as sp
 
-METRICS = [(2, 2), (302, 3), (303, 3), (55, 2), (55, 3), (30355, 3)]
+METRICS = [(2, 2), (302, 3), (303, 3), (55, 2), (55, 3), (30355, 3),
+           (7, 2), (7, 3), (9, 2), (9, 3)]
 
 
 def _mu_def(mid, T):
@@ -26,6 +28,10 @@ def _mu_def(mid, T):
         return (tau - 1) ** 2
     if mid == 30355:
         return _mu_def(303, T) + _mu_def(55, T)
+    if mid in (7, 9):
+        R = T - np.linalg.inv(T).T
+        n2 = np.sum(R * R)
+        return n2 if mid == 7 else tau * n2
     raise ValueError(mid)
 
 
@@ -70,6 +76,11 @@ def _sym_mu(mid, d):
         mu = (tau - 1) ** 2
     elif mid == 30355:
         mu = I1 / (3 * tau ** sp.Rational(2, 3)) - 1 + (tau - 1) ** 2
+    elif mid in (7, 9):
+        R = Ts - (Ts.adjugate() / tau).T
+        mu = sum(R[i, j] ** 2 for i in range(d) for j in range(d))
+        if mid == 9:
+            mu = tau * mu
     syms = [Ts[i, j] for i in range(d) for j in range(d)]
     return syms, mu
 
@@ -105,6 +116,35 @@ def test_hand_values(oracle_mod):
         assert abs(mu - ((a * a + 2) * (a ** -2 + 2) / 9 - 1)) < 1e-14
         _, mu, _, _ = oracle_mod.metric(55, np.diag([a, 1.0, 1.0]))
         assert abs(mu - (a - 1) ** 2) < 1e-15
+        for d in (2, 3):
+            # stretch diag(a, 1, ..): T - T^-t = diag(a - 1/a, 0, ..)
+            _, mu, _, _ = oracle_mod.metric(7, np.diag([a] + [1.0] * (d - 1)))
+            assert abs(mu - (a - 1 / a) ** 2) < 1e-14
+            _, mu, _, _ = oracle_mod.metric(9, np.diag([a] + [1.0] * (d - 1)))
+            assert abs(mu - a * (a - 1 / a) ** 2) < 1e-14
+            # uniform scaling c I: |T - T^-t|^2 = d (c - 1/c)^2
+            _, mu, _, _ = oracle_mod.metric(7, a * np.eye(d))
+            assert abs(mu - d * (a - 1 / a) ** 2) < 1e-13
+            _, mu, _, _ = oracle_mod.metric(9, a * np.eye(d))
+            assert abs(mu - a ** d * d * (a - 1 / a) ** 2) < 1e-12
+
+
+@pytest.mark.parametrize("mid,d", [(7, 2), (7, 3), (9, 2), (9, 3)])
+def test_shape_size_metric_invariance_and_minimum(oracle_mod, mid, d):
+    """mu_7, mu_9 are >= 0, vanish exactly on rotations (T^T T = I), are
+    invariant under T -> R T Q but not under scaling (they see size)."""
+    from paper_2205_12721_b300.meshgen import random_rotation
+    rng = np.random.default_rng(8)
+    for k, T in enumerate(_random_T(d, rng)):
+        _, mu, _, _ = oracle_mod.metric(mid, T)
+        assert mu >= 0
+        R, Q = random_rotation(d, 30 + k), random_rotation(d, 40 + k)
+        _, mu2, _, _ = oracle_mod.metric(mid, R @ T @ Q)
+        assert abs(mu2 - mu) < 1e-13 * max(1, mu)
+        _, mu0, P0, _ = oracle_mod.metric(mid, R)
+        assert abs(mu0) < 1e-14 and np.abs(P0).max() < 1e-13
+        _, mus, _, _ = oracle_mod.metric(mid, 1.5 * R)
+        assert mus > 0.1
 
 
 @pytest.mark.parametrize("mid,d", [(2, 2), (302, 3), (303, 3)])
