@@ -60,9 +60,11 @@ typedef enum {
  *   TMOP_METRIC_302   (3D) mu = |T|^2 |T^-1|^2 / 9 - 1              shape
  *   TMOP_METRIC_303   (3D) mu = |T|^2 / (3 tau^(2/3)) - 1            shape
  *   TMOP_METRIC_55    (2D/3D) mu = (tau - 1)^2                       size
- *   TMOP_METRIC_303_55 (3D) mu_303 + mu_55                          shape+size */
-enum { TMOP_METRIC_2 = 2, TMOP_METRIC_55 = 55, TMOP_METRIC_302 = 302,
-       TMOP_METRIC_303 = 303, TMOP_METRIC_303_55 = 30355 };
+ *   TMOP_METRIC_303_55 (3D) mu_303 + mu_55                          shape+size
+ *   TMOP_METRIC_7     (2D/3D) mu = |T - T^-t|^2                      shape+size
+ *   TMOP_METRIC_9     (2D/3D) mu = tau |T - T^-t|^2                  shape+size */
+enum { TMOP_METRIC_2 = 2, TMOP_METRIC_7 = 7, TMOP_METRIC_9 = 9, TMOP_METRIC_55 = 55,
+       TMOP_METRIC_302 = 302, TMOP_METRIC_303 = 303, TMOP_METRIC_303_55 = 30355 };
 
 /* Targets W (eq. W).  IDENTITY: W = I.  SIZE_FIELD: W = h0 s(x)^(1/dim) I
  * with s(x) = 1 + 0.5 prod_k sin(2 pi x_k) evaluated at the current physical

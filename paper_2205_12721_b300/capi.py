@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libtmop_b300.so")
 OK, ERR_ARG, ERR_INVERTED, ERR_CUDA, ERR_OOM, ERR_MINRES, ERR_LINESEARCH, ERR_TIMEOUT, \
     ERR_UNSUPPORTED = range(9)
 METRIC_2, METRIC_55, METRIC_302, METRIC_303, METRIC_303_55 = 2, 55, 302, 303, 30355
+METRIC_7, METRIC_9 = 7, 9
 TARGET_IDENTITY, TARGET_SIZE_FIELD = 0, 1
 FP64, FP32, FP64_NATIVE = 0, 1, 2
 K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)

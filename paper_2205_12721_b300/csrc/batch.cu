@@ -702,10 +702,7 @@ tmop_status tmop_batch_create(const tmop_batch_desc *desc, void *cuda_stream, tm
     if (D.dim != 2 && D.dim != 3) return bfail(TMOP_ERR_ARG, "dim must be 2 or 3");
     if (!elem_supported(D.dim, D.order, D.nq1d))
         return bfail(TMOP_ERR_UNSUPPORTED, "order must be 1..4 and nq1d order+1, order+2 (or 9 in 3D)");
-    const bool mok = (D.metric == TMOP_METRIC_2 && D.dim == 2) ||
-                     ((D.metric == TMOP_METRIC_302 || D.metric == TMOP_METRIC_303 ||
-                       D.metric == TMOP_METRIC_303_55) && D.dim == 3) ||
-                     D.metric == TMOP_METRIC_55;
+    const bool mok = metric_valid(D.metric, D.dim);
     if (!mok) return bfail(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
     if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
         return bfail(TMOP_ERR_ARG, "unknown target");

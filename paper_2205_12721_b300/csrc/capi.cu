@@ -188,12 +188,7 @@ tmop_status prof_resolve(tmop_ctx *c)
     return TMOP_OK;
 }
 
-bool metric_ok(int m, int d)
-{
-    if (m == TMOP_METRIC_2) return d == 2;
-    if (m == TMOP_METRIC_302 || m == TMOP_METRIC_303 || m == TMOP_METRIC_303_55) return d == 3;
-    return m == TMOP_METRIC_55;
-}
+bool metric_ok(int m, int d) { return metric_valid(m, d); }
 
 tmop_status limit_ready(tmop_ctx *c)
 {

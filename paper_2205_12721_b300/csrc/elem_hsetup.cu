@@ -23,7 +23,7 @@ template <class C, class RS, class RH>
 static cudaError_t run_hsetup(const ElemParams &P, const double *x, RH *H, cudaStream_t s,
                               const BatchArgs &B, int64_t ntiles)
 {
-    if (C::D == 3 && P.metric == MET_302) return run_hsetup_m<C, RS, RH, true>(P, x, H, s, B, ntiles);
+    if (metric_uses_I2(P.metric, C::D)) return run_hsetup_m<C, RS, RH, true>(P, x, H, s, B, ntiles);
     return run_hsetup_m<C, RS, RH, false>(P, x, H, s, B, ntiles);
 }
 

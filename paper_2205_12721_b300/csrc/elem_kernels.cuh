@@ -182,7 +182,7 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
         emin = fmin(emin, detA);
         if (detA > 0.0) {
             Inv v;
-            esum += cq * metric_scalars(P.metric, I1, tau, I2, v);
+            esum += cq * metric_scalars<C::D>(P.metric, I1, tau, I2, v);
         }
     });
 
@@ -229,7 +229,7 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
             return;
         }
         Inv v;
-        esum += cq * metric_scalars(P.metric, I1, tau, I2, v);
+        esum += cq * metric_scalars<C::D>(P.metric, I1, tau, I2, v);
         if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
         const double sc = cq * iws;
 #pragma unroll
@@ -245,7 +245,8 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
 }
 
 // ---------------------------------------------------------------- Hessian setup
-// HAS_I2 = false: metrics of (I1, tau) only (mu_2, mu_303, mu_55, mu_303 + mu_55),
+// HAS_I2 = false: metrics of (I1, tau) only (mu_2, mu_303, mu_55, mu_303 + mu_55,
+// and the 2D mu_7, mu_9),
 // whose d2mu/dT2 is u (x) g1 + w (x) cof T + 2 f1 Id + f_tau d2tau with
 // u = f11 g1 + f1t cof T, w = f1t g1 + ftt cof T: two FMAs per stored entry.
 template <class C, class RS, class RH, bool HAS_I2>
@@ -283,7 +284,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
             return;
         }
         Inv v;
-        metric_scalars(P.metric, I1, tau, I2, v);
+        metric_scalars<C::D>(P.metric, I1, tau, I2, v);
         const double sc = cq * iws * iws;
         if constexpr (HAS_I2) {
             if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);

@@ -63,10 +63,7 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
     if (D.dim != 2 && D.dim != 3) return set_error(TMOP_ERR_ARG, "dim must be 2 or 3");
     if (!elem_supported(D.dim, D.order, D.nq1d))
         return set_error(TMOP_ERR_UNSUPPORTED, "order must be 1..4 and nq1d order+1, order+2 (or 9 in 3D)");
-    const bool metric_ok = (D.metric == TMOP_METRIC_2 && D.dim == 2) ||
-                           ((D.metric == TMOP_METRIC_302 || D.metric == TMOP_METRIC_303 ||
-                             D.metric == TMOP_METRIC_303_55) && D.dim == 3) ||
-                           D.metric == TMOP_METRIC_55;
+    const bool metric_ok = metric_valid(D.metric, D.dim);
     if (!metric_ok) return set_error(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
     if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
         return set_error(TMOP_ERR_ARG, "unknown target");

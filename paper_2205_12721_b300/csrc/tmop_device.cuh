@@ -17,7 +17,20 @@
 
 namespace tmop {
 
-enum { MET_2 = 2, MET_55 = 55, MET_302 = 302, MET_303 = 303, MET_303_55 = 30355 };
+enum { MET_2 = 2, MET_7 = 7, MET_9 = 9, MET_55 = 55, MET_302 = 302, MET_303 = 303,
+       MET_303_55 = 30355 };
+
+// Metric ids defined for dimension d, and those whose 3D form uses I2 = |cof T|^2.
+__host__ __device__ inline bool metric_valid(int m, int d)
+{
+    if (m == MET_2) return d == 2;
+    if (m == MET_302 || m == MET_303 || m == MET_303_55) return d == 3;
+    return m == MET_55 || m == MET_7 || m == MET_9;
+}
+__host__ __device__ inline bool metric_uses_I2(int m, int d)
+{
+    return d == 3 && (m == MET_302 || m == MET_7 || m == MET_9);
+}
 enum { TGT_IDENTITY = 0, TGT_SIZE = 1 };
 
 template <int D_, int P_, int Q_>
@@ -409,6 +422,10 @@ __device__ __forceinline__ void cofactor(const double *T, double *Cf)
 }
 
 // mu and the scalar derivatives for metric id at invariants (I1, tau, I2).
+// mu_7 = |T - T^-t|^2 = I1 - 2D + |T^-1|^2 (the cross term <T, T^-t> is
+// tr(T^-1 T) = D), with |T^-1|^2 = I2 / tau^2 in 3D and I1 / tau^2 in 2D;
+// mu_9 = tau mu_7.
+template <int D>
 __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, double I2, Inv &v)
 {
     v.f1 = v.ft = v.f2 = v.f11 = v.f1t = v.ftt = v.f12 = v.f2t = 0.0;
@@ -430,6 +447,39 @@ __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, 
         v.f1t = -2.0 * I2 * it2 * it / 9.0;
         v.f2t = -2.0 * I1 * it2 * it / 9.0;
         v.ftt = 2.0 * I1 * I2 * it2 * it2 / 3.0;
+    } else if (id == MET_7 || id == MET_9) {
+        const double it2 = it * it;
+        const double J = (D == 3 ? I2 : I1) * it2;            // |T^-1|^2
+        if (id == MET_7) {
+            mu = I1 + J - 2.0 * D;
+            if (D == 3) {
+                v.f1 = 1.0;
+                v.f2 = it2;
+                v.ft = -2.0 * J * it;
+                v.f2t = -2.0 * it2 * it;
+                v.ftt = 6.0 * J * it2;
+            } else {
+                v.f1 = 1.0 + it2;
+                v.ft = -2.0 * J * it;
+                v.f1t = -2.0 * it2 * it;
+                v.ftt = 6.0 * J * it2;
+            }
+        } else {
+            mu = tau * (I1 + J - 2.0 * D);
+            if (D == 3) {
+                v.f1 = tau;
+                v.f2 = it;
+                v.ft = I1 - J - 6.0;
+                v.f1t = 1.0;
+                v.f2t = -it2;
+                v.ftt = 2.0 * J * it;
+            } else {
+                v.f1 = tau + it;
+                v.ft = I1 - J - 4.0;
+                v.f1t = 1.0 - it2;
+                v.ftt = 2.0 * J * it;
+            }
+        }
     } else {
         if (id == MET_303 || id == MET_303_55) {
             const double cr = cbrt(tau);

@@ -26,7 +26,10 @@ for p in (1, 2, 3, 4):
 CASES += [(2, 2, 3, 55, 0), (3, 2, 3, 55, 0), (3, 3, 4, 30355, 1), (3, 1, 2, 30355, 1),
           (3, 4, 5, 30355, 1), (2, 3, 4, 55, 1), (3, 2, 3, 302, 1),
           # the 9^3-point rule of the paper's Kershaw runs
-          (3, 1, 9, 303, 0), (3, 2, 9, 302, 0), (3, 4, 9, 303, 0)]
+          (3, 1, 9, 303, 0), (3, 2, 9, 302, 0), (3, 4, 9, 303, 0),
+          # shape+size metrics mu_7 = |T - T^-t|^2, mu_9 = tau |T - T^-t|^2
+          (2, 2, 3, 7, 1), (2, 3, 4, 9, 0), (2, 1, 3, 9, 1), (3, 2, 3, 7, 1), (3, 3, 4, 9, 1),
+          (3, 1, 2, 7, 0), (3, 4, 5, 9, 1)]
 
 
 def _ids(c):
@@ -34,7 +37,8 @@ def _ids(c):
 
 
 NATIVE_CASES = [(2, 2, 3, 2, 0), (2, 4, 6, 2, 0), (3, 1, 2, 302, 0), (3, 3, 4, 303, 0),
-                (3, 4, 5, 302, 0), (3, 2, 3, 30355, 1), (3, 3, 9, 303, 0)]
+                (3, 4, 5, 302, 0), (3, 2, 3, 30355, 1), (3, 3, 9, 303, 0), (3, 2, 3, 9, 1),
+                (2, 2, 3, 7, 1)]
 PARAMS = [(c, "fp64") for c in CASES] + [(c, "fp64-native") for c in NATIVE_CASES]
 
 
@@ -76,7 +80,8 @@ def test_fp64_parity(case, precision):
 
 
 @pytest.mark.parametrize("case", [(2, 2, 3, 2, 0), (3, 2, 3, 302, 0), (3, 3, 4, 303, 0),
-                                  (3, 4, 5, 303, 0), (3, 2, 3, 30355, 1)], ids=_ids)
+                                  (3, 4, 5, 303, 0), (3, 2, 3, 30355, 1), (3, 3, 4, 7, 1)],
+                         ids=_ids)
 def test_fp32_hessian_data(case):
     """FP32 stored d2mu/dT2 and FP32 action: error stated against the FP64
     oracle (single-precision rounding of H, v and the contractions)."""
@@ -197,6 +202,17 @@ def test_newton_iterates_3d():
     _newton_parity(mg.perturb_smooth(mg.structured(3, 3, (4, 3, 3)), 5, 0.03, 0.015), 303, 3)
     _newton_parity(mg.perturb_smooth(mg.structured(3, 2, 4), 6, 0.03, 0.015), 30355, 3,
                    target=1, h0=0.25)
+
+
+def test_newton_iterates_shape_size_metrics():
+    """mu_7 and mu_9 with the size target (their 3D forms use I2 = |cof T|^2)."""
+    from paper_2205_12721_b300 import meshgen as mg
+    _newton_parity(mg.perturb_smooth(mg.structured(3, 2, 4), 7, 0.03, 0.015), 7, 3,
+                   target=1, h0=0.25)
+    _newton_parity(mg.perturb_smooth(mg.structured(3, 3, (3, 3, 4)), 8, 0.03, 0.015), 9, 3,
+                   target=1, h0=0.25)
+    _newton_parity(mg.perturb_smooth(mg.structured(2, 3, 6), 9, 0.05, 0.02), 9, 3,
+                   target=1, h0=1.0 / 6)
 
 
 def test_cfg1_solve_reaches_uniform_mesh():
