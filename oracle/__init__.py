@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "tmop_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, ERR_ARG, ERR_INVERTED, ERR_MINRES, ERR_LINESEARCH = 0, 1, 2, 5, 6
-TARGET_IDENTITY, TARGET_SIZE = 0, 1
+TARGET_IDENTITY, TARGET_SIZE, TARGET_DISCRETE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -42,6 +42,9 @@ class _Mesh(ctypes.Structure):
         ("metric", ctypes.c_int), ("target", ctypes.c_int), ("target_h0", ctypes.c_double),
         ("map", ctypes.c_void_p), ("fixed", ctypes.c_void_p),
         ("limit_delta", ctypes.c_double), ("x0", ctypes.c_void_p),
+        ("eta", ctypes.c_void_p), ("remap_x0", ctypes.c_void_p), ("remap_eta0", ctypes.c_void_p),
+        ("remap_steps", ctypes.c_int), ("remap_cg_max_it", ctypes.c_int),
+        ("remap_cg_rtol", ctypes.c_double),
     ]
 
 
@@ -78,6 +81,10 @@ def lib():
             "or_hessian_apply_cached": (I, [P, P, P, P, P]),
             "or_minres": (I, [P, P, P, P, P, D, I, I, P, P, P]),
             "or_newton_step": (I, [P, P, D, I, I, D, I, P]),
+            "or_mass_apply": (I, [P, P, P, P]),
+            "or_mass_diag": (I, [P, P, P]),
+            "or_advect_apply": (I, [P, P, P, P, P]),
+            "or_remap": (I, [P, P, P, P, I, D, I, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -139,16 +146,30 @@ class Mesh:
     target_h0: float = 1.0
     limit_delta: float = 0.0           # > 0 with x0: limiting term |x - x0|^2 / delta^2
     x0: np.ndarray | None = None
+    eta: np.ndarray | None = None      # discrete target: nodal field on the current mesh
+    remap_x0: np.ndarray | None = None  # Newton: eta remapped from (remap_x0, remap_eta0)
+    remap_eta0: np.ndarray | None = None
+    remap_steps: int = 4
+    remap_cg_max_it: int = 200
+    remap_cg_rtol: float = 1e-12
 
     def __post_init__(self):
         self.map = np.ascontiguousarray(self.map, dtype=np.int32)
         if self.fixed is not None:
             self.fixed = np.ascontiguousarray(self.fixed, dtype=np.uint8)
-        if self.x0 is not None:
-            self.x0 = np.ascontiguousarray(self.x0, dtype=np.float64)
+        for f in ("x0", "eta", "remap_x0", "remap_eta0"):
+            if getattr(self, f) is not None:
+                setattr(self, f, np.ascontiguousarray(getattr(self, f), dtype=np.float64))
         self._c = _Mesh(self.dim, self.order, self.nq1d, self.map.shape[0], self.num_nodes,
                         self.metric, self.target, self.target_h0, _p(self.map), _p(self.fixed),
-                        self.limit_delta, _p(self.x0))
+                        self.limit_delta, _p(self.x0), _p(self.eta), _p(self.remap_x0),
+                        _p(self.remap_eta0), self.remap_steps, self.remap_cg_max_it,
+                        self.remap_cg_rtol)
+
+    def set_eta(self, eta):
+        """Replace the discrete target field (nodal values on the current mesh)."""
+        self.eta = np.ascontiguousarray(eta, dtype=np.float64)
+        self._c.eta = _p(self.eta)
 
     @property
     def ndof(self):
@@ -253,3 +274,37 @@ def newton_step(m: Mesh, x, minres_rtol=1e-8, minres_max_it=50, minres_fixed_its
     lib().or_newton_step(m.ref(), _p(x), minres_rtol, minres_max_it, int(minres_fixed_its),
                          ls_factor, ls_max_halvings, ctypes.byref(r))
     return {f: getattr(r, f) for f, _ in _Report._fields_}
+
+
+# ---------------------------------------------------------------- remap (Sec. 3.6)
+def mass_apply(m: Mesh, x, u):
+    """(status, M(x) u) for a nodal scalar field u."""
+    x = _f64(x); u = _f64(u)
+    y = np.zeros(m.num_nodes)
+    st = lib().or_mass_apply(m.ref(), _p(x), _p(u), _p(y))
+    return st, y
+
+
+def mass_diag(m: Mesh, x):
+    x = _f64(x)
+    dg = np.zeros(m.num_nodes)
+    st = lib().or_mass_diag(m.ref(), _p(x), _p(dg))
+    return st, dg
+
+
+def advect_apply(m: Mesh, x, vel, u):
+    """(status, K(x, vel) u): int w_i vel . grad u over the mesh x."""
+    x = _f64(x); vel = _f64(vel); u = _f64(u)
+    y = np.zeros(m.num_nodes)
+    st = lib().or_advect_apply(m.ref(), _p(x), _p(vel), _p(u), _p(y))
+    return st, y
+
+
+def remap(m: Mesh, x0, x1, eta0, steps=4, cg_rtol=1e-12, cg_max_it=200):
+    """(status, eta1, total CG iterations): eta0 on x0 advected to x1."""
+    x0 = _f64(x0); x1 = _f64(x1); eta0 = _f64(eta0)
+    eta1 = np.zeros(m.num_nodes)
+    its = ctypes.c_int(0)
+    st = lib().or_remap(m.ref(), _p(x0), _p(x1), _p(eta0), int(steps), float(cg_rtol),
+                        int(cg_max_it), _p(eta1), ctypes.byref(its))
+    return st, eta1, its.value

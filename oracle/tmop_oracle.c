@@ -37,7 +37,7 @@
 
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_INVERTED = 2, OR_ERR_MINRES = 5,
        OR_ERR_LINESEARCH = 6 };
-enum { OR_TARGET_IDENTITY = 0, OR_TARGET_SIZE = 1 };
+enum { OR_TARGET_IDENTITY = 0, OR_TARGET_SIZE = 1, OR_TARGET_DISCRETE = 2 };
 
 /* ------------------------------------------------------------------------
  * 1D quadrature and basis (Sec. 3.1, eq. B_G_1D)
@@ -385,6 +385,12 @@ typedef struct {
     const uint8_t *fixed;      /* dim*num_nodes, or NULL */
     double limit_delta;        /* > 0: limiting term xi = |x - x0|^2 / delta^2 (Sec. 3.5) */
     const double *x0;          /* reference positions of the limiting term */
+    const double *eta;         /* discrete target: nodal field eta[node] on the current mesh */
+    /* Newton with the discrete target: eta is remapped from (remap_x0,
+     * remap_eta0) to every new position (Sec. 3.6) when remap_eta0 != NULL */
+    const double *remap_x0, *remap_eta0;
+    int remap_steps, remap_cg_max_it;
+    double remap_cg_rtol;
 } or_mesh;
 
 typedef struct {
@@ -438,10 +444,14 @@ static double size_field(int d, const double *xq)
     return 1.0 + s;
 }
 
-/* Target matrix W at a quadrature point (eq. W; Sec. 3.6: recomputed from the
- * current positions, derivative terms dW/dx dropped).  Returns det W and W^-1. */
-static double target_at(const or_mesh *M, const or_tables *t, const double *xw_e, int q,
-                        double *Winv)
+/* Target matrix W at a quadrature point of element e (eq. W; Sec. 3.6:
+ * recomputed from the current positions, derivative terms dW/dx dropped).
+ * Size target: W = h0 s(x_q)^(1/d) I.  Discrete target: W = h0 eta(x_q)^(1/d) I
+ * with eta(x_q) = sum_i eta_i w_i(chi_q), the interpolated nodal field; it
+ * needs eta(x_q) > 0, else W is undefined and det W is returned as NaN (the
+ * callers then treat the point as inverted).  Returns det W and W^-1. */
+static double target_at(const or_mesh *M, const or_tables *t, int64_t e, const double *xw_e,
+                        int q, double *Winv)
 {
     int d = t->d;
     double w = 1.0;
@@ -450,6 +460,14 @@ static double target_at(const or_mesh *M, const or_tables *t, const double *xw_e
         for (int a = 0; a < d; ++a)
             for (int i = 0; i < t->np; ++i) xq[a] += xw_e[a * t->np + i] * t->phi[q * t->np + i];
         w = M->target_h0 * pow(size_field(d, xq), 1.0 / d);
+    } else if (M->target == OR_TARGET_DISCRETE) {
+        double eq = 0;
+        for (int i = 0; i < t->np; ++i) eq += M->eta[M->map[e * t->np + i]] * t->phi[q * t->np + i];
+        if (!(eq > 0)) {
+            for (int k = 0; k < d * d; ++k) Winv[k] = NAN;
+            return NAN;
+        }
+        w = M->target_h0 * pow(eq, 1.0 / d);
     }
     double W[9] = {0};
     for (int a = 0; a < d; ++a) W[a * d + a] = w;
@@ -529,7 +547,8 @@ int or_energy(const or_mesh *M, const double *x, const double *xw, const int64_t
             jacobian(&t, xe, q, A);
             double detA = det_def(d, A);
             if (detA < mind) mind = detA;
-            double detW = target_at(M, &t, xwe, q, Winv);
+            double detW = target_at(M, &t, e, xwe, q, Winv);
+            if (!(detW > 0)) { inverted = 1; mind = -INFINITY; continue; }   /* undefined target */
             matmul(d, A, Winv, T);
             double c = t.w[q] * detW;
             S += fabs(c);
@@ -604,7 +623,8 @@ int or_gradient(const or_mesh *M, const double *x, const double *xw, const int64
         for (int q = 0; q < t.nqd; ++q) {
             double A[9], Winv[9], T[9], P[9], mu;
             jacobian(&t, xe, q, A);
-            double detW = target_at(M, &t, xwe, q, Winv);
+            double detW = target_at(M, &t, e, xwe, q, Winv);
+            if (!(detW > 0)) { rc = OR_ERR_INVERTED; continue; }
             matmul(d, A, Winv, T);
             if (limiting_on(M)) {          /* d/dx_{a,i}: c 2 (x - x0)_a w_i / delta^2 */
                 double xq[3], x0q[3], c2 = t.w[q] * detW * 2.0 / (M->limit_delta * M->limit_delta);
@@ -650,12 +670,15 @@ int or_gradient(const or_mesh *M, const double *x, const double *xw, const int64
 
 /* H^A_{ab,ce} = w_q det W sum_{n,f} K_{an,cf} W^-1_{bn} W^-1_{ef}: the
  * A-space second derivative at one point (eq. vm_pa_hess with a general W). */
-static int hess_A(const or_mesh *M, const or_tables *t, const double *xe, int q, double *HA)
+static int hess_A(const or_mesh *M, const or_tables *t, int64_t e, const double *xe, int q,
+                  double *HA)
 {
     int d = t->d, dd = d * d;
     double A[9], Winv[9], T[9], K[81], mu;
+    memset(HA, 0, sizeof(double) * dd * dd);
     jacobian(t, xe, q, A);
-    double detW = target_at(M, t, xe, q, Winv);
+    double detW = target_at(M, t, e, xe, q, Winv);
+    if (!(detW > 0)) return OR_ERR_INVERTED;
     matmul(d, A, Winv, T);
     int st = or_metric(M->metric, d, T, &mu, NULL, K);
     if (st != OR_OK) return st;
@@ -663,12 +686,12 @@ static int hess_A(const or_mesh *M, const or_tables *t, const double *xe, int q,
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b)
             for (int cc = 0; cc < d; ++cc)
-                for (int e = 0; e < d; ++e) {
+                for (int ee = 0; ee < d; ++ee) {
                     double s = 0;
                     for (int n = 0; n < d; ++n)
                         for (int f = 0; f < d; ++f)
-                            s += K[(a * d + n) * dd + cc * d + f] * Winv[b * d + n] * Winv[e * d + f];
-                    HA[(a * d + b) * dd + cc * d + e] = c * s;
+                            s += K[(a * d + n) * dd + cc * d + f] * Winv[b * d + n] * Winv[ee * d + f];
+                    HA[(a * d + b) * dd + cc * d + ee] = c * s;
                 }
     return OR_OK;
 }
@@ -703,9 +726,11 @@ static int hessian_apply_impl(const or_mesh *M, const double *x, const double *v
                 ve[a * t.np + i] = (M->fixed && M->fixed[j]) ? 0.0 : v[j];
             }
         for (int q = 0; q < t.nqd; ++q) {
+            double Winv0[9];
+            if (!(target_at(M, &t, e, xe, q, Winv0) > 0)) { rc = OR_ERR_INVERTED; continue; }
             if (limiting_on(M)) {          /* eq. pa_limiting: c 2/delta^2 w_i sum_j v_{a,j} w_j */
                 double Winv[9], vq[3];
-                double c2 = t.w[q] * target_at(M, &t, xe, q, Winv) * 2.0 /
+                double c2 = t.w[q] * target_at(M, &t, e, xe, q, Winv) * 2.0 /
                             (M->limit_delta * M->limit_delta);
                 interp(&t, ve, q, vq);
                 for (int i = 0; i < t.np; ++i) {
@@ -720,7 +745,7 @@ static int hessian_apply_impl(const or_mesh *M, const double *x, const double *v
             double HAl[81];
             const double *HA = HAl;
             if (HAcache) HA = HAcache + ((int64_t)e * t.nqd + q) * dd * dd;
-            else if (hess_A(M, &t, xe, q, HAl) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
+            else if (hess_A(M, &t, e, xe, q, HAl) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
             double dA[9], Y[9], aY[9];
             jacobian(&t, ve, q, dA);
             for (int r = 0; r < dd; ++r) {
@@ -770,7 +795,7 @@ double *or_hess_cache_build(const or_mesh *M, const double *x, int *status)
     for (int64_t e = 0; e < M->num_elems; ++e) {
         gather_elem(M, &t, x, e, xe);
         for (int q = 0; q < t.nqd; ++q)
-            if (hess_A(M, &t, xe, q, H + (e * t.nqd + q) * dd * dd) != OR_OK) *status = OR_ERR_INVERTED;
+            if (hess_A(M, &t, e, xe, q, H + (e * t.nqd + q) * dd * dd) != OR_OK) *status = OR_ERR_INVERTED;
     }
     free(xe); tables_free(&t);
     return H;
@@ -804,9 +829,11 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
         int64_t e = elem_at(elems, k);
         gather_elem(M, &t, x, e, xe);
         for (int q = 0; q < t.nqd; ++q) {
+            double Winv0[9];
+            if (!(target_at(M, &t, e, xe, q, Winv0) > 0)) { rc = OR_ERR_INVERTED; continue; }
             if (limiting_on(M)) {          /* c 2/delta^2 w_i^2 */
                 double Winv[9];
-                double c2 = t.w[q] * target_at(M, &t, xe, q, Winv) * 2.0 /
+                double c2 = t.w[q] * target_at(M, &t, e, xe, q, Winv) * 2.0 /
                             (M->limit_delta * M->limit_delta);
                 for (int i = 0; i < t.np; ++i) {
                     int64_t node = M->map[e * t.np + i];
@@ -815,7 +842,7 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
                 }
             }
             double HA[81];
-            if (hess_A(M, &t, xe, q, HA) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
+            if (hess_A(M, &t, e, xe, q, HA) != OR_OK) { rc = OR_ERR_INVERTED; continue; }
             for (int i = 0; i < t.np; ++i) {
                 int64_t node = M->map[e * t.np + i];
                 const double *gi = t.dphi + (q * t.np + i) * d;
@@ -930,6 +957,186 @@ int or_minres(const or_mesh *M, const double *x, const double *HA, const double 
  * F(x+) < ls_factor F(x) and |dF(x+)| < ls_factor |dF(x)|.  x is overwritten
  * only when a step is accepted.
  * --------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------
+ * Adaptive discrete target and its advection remap (Sec. 3.6)
+ *
+ * The discrete target reads a finite element field eta of the mesh's own
+ * space (nodal values eta[node]).  The field is given on positions x0; on
+ * positions x1 its values come from the pseudo-time advection
+ *     d eta / dt = v . grad eta,   v = x1 - x0,   x_t = x0 + t v,  t in [0, 1],
+ * discretised by Galerkin in the same space, whose basis functions move with
+ * the nodes:
+ *     M(x_t) d eta/dt = K(x_t) eta,
+ *     M_ij = int w_i w_j dx,   K_ij = int w_i v . grad_x w_j dx   (mesh x_t),
+ * integrated with the mesh's quadrature rule (grad_x = A^-T grad_xbar).
+ * Pseudo-time integration: the classical fourth-order Runge-Kutta method with
+ * n uniform steps; every stage solves M k = K eta with Jacobi-preconditioned
+ * CG from a zero initial guess.
+ * --------------------------------------------------------------------- */
+
+static void gather_scalar(const or_mesh *M, const or_tables *t, const double *u, int64_t e, double *ue)
+{
+    for (int i = 0; i < t->np; ++i) ue[i] = u[M->map[e * t->np + i]];
+}
+
+/* y = M(x) u, y_i = sum_E sum_q w_q det A_q w_i(chi_q) u(chi_q).  Returns
+ * OR_ERR_INVERTED (after computing y) when det A <= 0 at some point. */
+int or_mass_apply(const or_mesh *M, const double *x, const double *u, double *y)
+{
+    or_tables t;
+    int st = tables_build(M, &t);
+    if (st) return st;
+    int d = t.d, rc = OR_OK;
+    memset(y, 0, sizeof(double) * M->num_nodes);
+    double *xe = malloc(sizeof(double) * d * t.np), *ue = malloc(sizeof(double) * t.np);
+    for (int64_t e = 0; e < M->num_elems; ++e) {
+        gather_elem(M, &t, x, e, xe);
+        gather_scalar(M, &t, u, e, ue);
+        for (int q = 0; q < t.nqd; ++q) {
+            double A[9], uq = 0;
+            jacobian(&t, xe, q, A);
+            double detA = det_def(d, A);
+            if (!(detA > 0)) rc = OR_ERR_INVERTED;
+            for (int j = 0; j < t.np; ++j) uq += ue[j] * t.phi[q * t.np + j];
+            double c = t.w[q] * detA * uq;
+            for (int i = 0; i < t.np; ++i) y[M->map[e * t.np + i]] += c * t.phi[q * t.np + i];
+        }
+    }
+    free(xe); free(ue); tables_free(&t);
+    return rc;
+}
+
+/* diag M(x), sum_E sum_q w_q det A_q w_i(chi_q)^2. */
+int or_mass_diag(const or_mesh *M, const double *x, double *diag)
+{
+    or_tables t;
+    int st = tables_build(M, &t);
+    if (st) return st;
+    int d = t.d, rc = OR_OK;
+    memset(diag, 0, sizeof(double) * M->num_nodes);
+    double *xe = malloc(sizeof(double) * d * t.np);
+    for (int64_t e = 0; e < M->num_elems; ++e) {
+        gather_elem(M, &t, x, e, xe);
+        for (int q = 0; q < t.nqd; ++q) {
+            double A[9];
+            jacobian(&t, xe, q, A);
+            double detA = det_def(d, A);
+            if (!(detA > 0)) rc = OR_ERR_INVERTED;
+            for (int i = 0; i < t.np; ++i) {
+                double ph = t.phi[q * t.np + i];
+                diag[M->map[e * t.np + i]] += t.w[q] * detA * ph * ph;
+            }
+        }
+    }
+    free(xe); tables_free(&t);
+    return rc;
+}
+
+/* y = K(x, vel) u, y_i = sum_E sum_q w_q det A_q w_i(chi_q) vel(chi_q) . grad_x u(chi_q),
+ * grad_x u = A_q^-T grad_xbar u.  vel has the layout of x. */
+int or_advect_apply(const or_mesh *M, const double *x, const double *vel, const double *u, double *y)
+{
+    or_tables t;
+    int st = tables_build(M, &t);
+    if (st) return st;
+    int d = t.d, rc = OR_OK;
+    memset(y, 0, sizeof(double) * M->num_nodes);
+    double *xe = malloc(sizeof(double) * d * t.np), *ve = malloc(sizeof(double) * d * t.np);
+    double *ue = malloc(sizeof(double) * t.np);
+    for (int64_t e = 0; e < M->num_elems; ++e) {
+        gather_elem(M, &t, x, e, xe);
+        gather_elem(M, &t, vel, e, ve);
+        gather_scalar(M, &t, u, e, ue);
+        for (int q = 0; q < t.nqd; ++q) {
+            double A[9], Ai[9], vq[3], gref[3] = {0, 0, 0}, gx[3];
+            jacobian(&t, xe, q, A);
+            double detA = inv_def(d, A, Ai);
+            if (!(detA > 0)) { rc = OR_ERR_INVERTED; continue; }
+            interp(&t, ve, q, vq);
+            for (int j = 0; j < t.np; ++j)
+                for (int b = 0; b < d; ++b) gref[b] += ue[j] * t.dphi[(q * t.np + j) * d + b];
+            double vg = 0;
+            for (int a = 0; a < d; ++a) {          /* (A^-T gref)_a = sum_b Ai_ba gref_b */
+                gx[a] = 0;
+                for (int b = 0; b < d; ++b) gx[a] += Ai[b * d + a] * gref[b];
+                vg += vq[a] * gx[a];
+            }
+            double c = t.w[q] * detA * vg;
+            for (int i = 0; i < t.np; ++i) y[M->map[e * t.np + i]] += c * t.phi[q * t.np + i];
+        }
+    }
+    free(xe); free(ve); free(ue); tables_free(&t);
+    return rc;
+}
+
+/* Jacobi-preconditioned CG for M(x) k = b from k = 0.  Stops when
+ * sqrt(r.z) <= rtol sqrt(b.D^-1 b) (z = D^-1 r) or after max_it iterations;
+ * returns the iterations done. */
+static int mass_cg(const or_mesh *M, const double *x, const double *diag, const double *b,
+                   double rtol, int max_it, double *k)
+{
+    int64_t n = M->num_nodes;
+    double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n), *Mp = malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i) { k[i] = 0; r[i] = b[i]; z[i] = r[i] / diag[i]; p[i] = z[i]; }
+    double rz = dotv(n, r, z), stop = rtol * rtol * rz;
+    int it = 0;
+    while (it < max_it && rz > stop && rz > 0) {
+        or_mass_apply(M, x, p, Mp);
+        double alpha = rz / dotv(n, p, Mp);
+        for (int64_t i = 0; i < n; ++i) { k[i] += alpha * p[i]; r[i] -= alpha * Mp[i]; z[i] = r[i] / diag[i]; }
+        double rz1 = dotv(n, r, z);
+        double beta = rz1 / rz;
+        rz = rz1;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        ++it;
+    }
+    free(r); free(z); free(p); free(Mp);
+    return it;
+}
+
+/* eta1 = eta0 advected from positions x0 to x1 (see above).  cg_its (optional)
+ * receives the total CG iterations.  Returns OR_ERR_INVERTED when an
+ * intermediate mesh x_t has det A <= 0 at some point (eta1 then undefined). */
+int or_remap(const or_mesh *M, const double *x0, const double *x1, const double *eta0, int nsteps,
+             double cg_rtol, int cg_max_it, double *eta1, int *cg_its)
+{
+    if (nsteps < 1) return OR_ERR_ARG;
+    int64_t Nx = M->num_nodes, nd = (int64_t)M->dim * Nx;
+    double *v = malloc(sizeof(double) * nd), *xt = malloc(sizeof(double) * nd);
+    double *diag = malloc(sizeof(double) * Nx), *rhs = malloc(sizeof(double) * Nx);
+    double *es = malloc(sizeof(double) * Nx), *kk[4];
+    for (int s = 0; s < 4; ++s) kk[s] = malloc(sizeof(double) * Nx);
+    for (int64_t i = 0; i < nd; ++i) v[i] = x1[i] - x0[i];
+    memcpy(eta1, eta0, sizeof(double) * Nx);
+    const double dt = 1.0 / nsteps;
+    const double cst[4] = {0.0, 0.5, 0.5, 1.0};      /* stage times (fractions of dt) */
+    const double ast[4] = {0.0, 0.5, 0.5, 1.0};      /* stage increments a_{s,s-1} */
+    int rc = OR_OK, total = 0;
+    for (int n = 0; n < nsteps && rc == OR_OK; ++n) {
+        for (int s = 0; s < 4; ++s) {
+            double tt = (n + cst[s]) * dt;
+            for (int64_t i = 0; i < nd; ++i) xt[i] = x0[i] + tt * v[i];
+            for (int64_t i = 0; i < Nx; ++i) es[i] = eta1[i] + (s ? ast[s] * dt * kk[s - 1][i] : 0.0);
+            if (or_mass_diag(M, xt, diag) != OR_OK) { rc = OR_ERR_INVERTED; break; }
+            or_advect_apply(M, xt, v, es, rhs);
+            total += mass_cg(M, xt, diag, rhs, cg_rtol, cg_max_it, kk[s]);
+        }
+        if (rc != OR_OK) break;
+        for (int64_t i = 0; i < Nx; ++i)
+            eta1[i] += dt / 6.0 * (kk[0][i] + 2.0 * kk[1][i] + 2.0 * kk[2][i] + kk[3][i]);
+    }
+    if (cg_its) *cg_its = total;
+    free(v); free(xt); free(diag); free(rhs); free(es);
+    for (int s = 0; s < 4; ++s) free(kk[s]);
+    return rc;
+}
+
+static int remap_on(const or_mesh *M)
+{
+    return M->target == OR_TARGET_DISCRETE && M->remap_eta0 != NULL && M->remap_x0 != NULL;
+}
+
 typedef struct {
     double energy, grad_norm, energy_new, grad_norm_new, alpha, min_det, minres_resid;
     int minres_iters, halvings, status;
@@ -940,10 +1147,24 @@ int or_newton_step(const or_mesh *M, double *x, double minres_rtol, int minres_m
 {
     int64_t n = (int64_t)M->dim * M->num_nodes;
     memset(rep, 0, sizeof(*rep));
+    /* discrete target with a remap source: eta follows every position change
+     * (Sec. 3.6), at x and at each line-search trial */
+    or_mesh Mx = *M, Mt = *M;
+    double *eta_x = NULL, *eta_t = NULL;
+    if (remap_on(M)) {
+        eta_x = malloc(sizeof(double) * M->num_nodes);
+        eta_t = malloc(sizeof(double) * M->num_nodes);
+        int rst = or_remap(M, M->remap_x0, x, M->remap_eta0, M->remap_steps, M->remap_cg_rtol,
+                           M->remap_cg_max_it, eta_x, NULL);
+        if (rst) { free(eta_x); free(eta_t); rep->status = rst; return rst; }
+        Mx.eta = eta_x;
+        Mt.eta = eta_t;
+    }
+    M = &Mx;
     double F0, mind;
     int st = or_energy(M, x, NULL, NULL, 0, &F0, &mind, NULL);
     rep->energy = F0; rep->min_det = mind;
-    if (st) { rep->status = st; return st; }
+    if (st) { rep->status = st; free(eta_x); free(eta_t); return st; }
     double *g = malloc(sizeof(double) * n), *diag = malloc(sizeof(double) * n);
     double *dx = malloc(sizeof(double) * n), *xt = malloc(sizeof(double) * n);
     or_gradient(M, x, NULL, NULL, 0, g, NULL);
@@ -951,7 +1172,7 @@ int or_newton_step(const or_mesh *M, double *x, double minres_rtol, int minres_m
     rep->grad_norm = g0;
     if (g0 == 0) {               /* already stationary: nothing to solve */
         rep->energy_new = F0; rep->status = OR_OK;
-        free(g); free(diag); free(dx); free(xt);
+        free(g); free(diag); free(dx); free(xt); free(eta_x); free(eta_t);
         return OR_OK;
     }
     double *HA = or_hess_cache_build(M, x, &st);
@@ -967,10 +1188,17 @@ int or_newton_step(const or_mesh *M, double *x, double minres_rtol, int minres_m
         for (int h = 0; h <= ls_max_halvings; ++h, alpha *= 0.5) {
             for (int64_t i = 0; i < n; ++i) xt[i] = x[i] - alpha * dx[i];
             double F1, md1;
-            int est = or_energy(M, xt, NULL, NULL, 0, &F1, &md1, NULL);
+            const or_mesh *MT = M;
+            if (eta_t) {
+                if (or_remap(M, M->remap_x0, xt, M->remap_eta0, M->remap_steps, M->remap_cg_rtol,
+                             M->remap_cg_max_it, eta_t, NULL) != OR_OK)
+                    continue;                                   /* x_t inverted on the way */
+                MT = &Mt;
+            }
+            int est = or_energy(MT, xt, NULL, NULL, 0, &F1, &md1, NULL);
             if (est != OR_OK || !(md1 > 0)) continue;          /* det A > 0 */
             if (!(F1 < ls_factor * F0)) continue;               /* energy */
-            or_gradient(M, xt, NULL, NULL, 0, g, NULL);
+            or_gradient(MT, xt, NULL, NULL, 0, g, NULL);
             double g1 = sqrt(dotv(n, g, g));
             if (!(g1 < ls_factor * g0)) continue;               /* gradient */
             memcpy(x, xt, sizeof(double) * n);
@@ -983,6 +1211,6 @@ int or_newton_step(const or_mesh *M, double *x, double minres_rtol, int minres_m
         rc = mst;
     }
     rep->status = rc;
-    free(g); free(diag); free(dx); free(xt);
+    free(g); free(diag); free(dx); free(xt); free(eta_x); free(eta_t);
     return rc;
 }
