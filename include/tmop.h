@@ -69,8 +69,13 @@ enum { TMOP_METRIC_2 = 2, TMOP_METRIC_7 = 7, TMOP_METRIC_9 = 9, TMOP_METRIC_55 =
 /* Targets W (eq. W).  IDENTITY: W = I.  SIZE_FIELD: W = h0 s(x)^(1/dim) I
  * with s(x) = 1 + 0.5 prod_k sin(2 pi x_k) evaluated at the current physical
  * quadrature point; W is recomputed whenever positions change and dW/dx is
- * not differentiated (Sec. 3.6). */
-enum { TMOP_TARGET_IDENTITY = 0, TMOP_TARGET_SIZE_FIELD = 1 };
+ * not differentiated (Sec. 3.6).  DISCRETE: W = h0 eta(x_q)^(1/dim) I with
+ * eta a finite element field of the mesh's own space (nodal values, one per
+ * node), interpolated to the points by the same contractions as the
+ * positions (Sec. 3.6); eta is set by tmop_set_target_field, or remapped to
+ * every new position by tmop_newton_step after tmop_set_remap_source.  A
+ * point with eta(x_q) <= 0 has no target and counts as inverted. */
+enum { TMOP_TARGET_IDENTITY = 0, TMOP_TARGET_SIZE_FIELD = 1, TMOP_TARGET_DISCRETE = 2 };
 
 /* Precision of the stored d2mu/dT2 data, the Hessian action, its diagonal
  * and the inner MINRES vectors.  Energy, gradient, det(A), the line search
@@ -93,7 +98,7 @@ typedef struct {
     int64_t num_nodes;   /* N_x */
     int metric;          /* TMOP_METRIC_* valid for dim */
     int target;          /* TMOP_TARGET_* */
-    double target_h0;    /* h0 of the size target (ignored for IDENTITY) */
+    double target_h0;    /* h0 of the size and discrete targets (ignored for IDENTITY) */
     int hess_precision;  /* TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE */
     double limit_delta;  /* > 0: add the limiting term |x - x0|^2 / delta^2 (Sec. 3.5,
                             eq. F_full); x0 is given by tmop_set_limit_reference.  0: off */
@@ -288,6 +293,56 @@ void tmop_batch_destroy(tmop_batch *b);
  * any evaluation of a context created with limit_delta > 0; TMOP_ERR_ARG
  * for a context without the term.  Asynchronous. */
 tmop_status tmop_set_limit_reference(tmop_ctx *ctx, const double *x0);
+
+/* ---------------------------------------------------------------------------
+ * Adaptive discrete target and its advection remap (Sec. 3.6).
+ *
+ * eta is known on positions x0; its values on positions x1 follow from the
+ * pseudo-time advection d eta/dt = v . grad eta, v = x1 - x0,
+ * x_t = x0 + t v, t in [0, 1], discretised by Galerkin in the mesh's space:
+ *     M(x_t) d eta/dt = K(x_t) eta,  M_ij = int w_i w_j,
+ *     K_ij = int w_i v . grad w_j  (on the mesh x_t, the mesh's quadrature),
+ * with the partially assembled mass and advection operators (w_q det A_q
+ * and w_q adj(A_q) v_q stored per point) and classical RK4 with `steps`
+ * uniform steps; every stage solves M k = K eta by Jacobi-preconditioned CG
+ * from k = 0, stopping when sqrt(r.z) <= cg_rtol sqrt(b.z0) or after
+ * cg_max_it iterations.  All arithmetic runs on the device; the host reads
+ * the CG stop flag once per chunk of iterations.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    int steps;           /* RK4 steps, >= 1 */
+    double cg_rtol;      /* relative preconditioned residual of the mass solves */
+    int cg_max_it;       /* >= 1 */
+} tmop_remap_opts;
+
+typedef struct {
+    int cg_iters;        /* CG iterations over all stages */
+    int solves;          /* mass solves (4 per step) */
+    double min_det;      /* min det A over the intermediate meshes x_t */
+    int status;          /* tmop_status */
+} tmop_remap_report;
+
+/* The field eta of a TMOP_TARGET_DISCRETE context on the current mesh.
+ * eta: device FP64, num_nodes values; copied.  Asynchronous.  TMOP_ERR_ARG
+ * for a context with another target. */
+tmop_status tmop_set_target_field(tmop_ctx *ctx, const double *eta);
+
+/* Remap source of a TMOP_TARGET_DISCRETE context: eta0 given on positions
+ * x0 (device FP64, num_nodes and dim * num_nodes values; copied).  From now
+ * on tmop_newton_step remaps eta from (x0, eta0) to x at its start and to
+ * every line-search trial (a trial whose intermediate mesh inverts is
+ * rejected); the field of the accepted positions stays in the context.
+ * eta0 = NULL switches the remap off.  opts NULL: {4, 1e-12, 200}. */
+tmop_status tmop_set_remap_source(tmop_ctx *ctx, const double *x0, const double *eta0,
+                                  const tmop_remap_opts *opts);
+
+/* eta1 = eta0 remapped from positions x0 to x1 on this context's mesh (any
+ * target).  Device FP64 pointers: x0, x1 dim * num_nodes; eta0, eta1
+ * num_nodes (eta1 may equal eta0).  Synchronous.  rep may be NULL.  Errors:
+ * TMOP_ERR_ARG, TMOP_ERR_INVERTED (det A <= 0 on some x_t; eta1 undefined),
+ * TMOP_ERR_OOM / TMOP_ERR_CUDA. */
+tmop_status tmop_remap(tmop_ctx *ctx, const double *x0, const double *x1, const double *eta0,
+                       double *eta1, const tmop_remap_opts *opts, tmop_remap_report *rep);
 
 /* Free the context and everything it owns.  NULL is accepted. */
 void tmop_destroy(tmop_ctx *ctx);

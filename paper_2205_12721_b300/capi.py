@@ -18,7 +18,7 @@ OK, ERR_ARG, ERR_INVERTED, ERR_CUDA, ERR_OOM, ERR_MINRES, ERR_LINESEARCH, ERR_TI
     ERR_UNSUPPORTED = range(9)
 METRIC_2, METRIC_55, METRIC_302, METRIC_303, METRIC_303_55 = 2, 55, 302, 303, 30355
 METRIC_7, METRIC_9 = 7, 9
-TARGET_IDENTITY, TARGET_SIZE_FIELD = 0, 1
+TARGET_IDENTITY, TARGET_SIZE_FIELD, TARGET_DISCRETE = 0, 1, 2
 FP64, FP32, FP64_NATIVE = 0, 1, 2
 K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)
 
@@ -29,7 +29,8 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc",
            "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
            "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
-           "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference")
+           "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference",
+           "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap")
 
 
 class TmopError(RuntimeError):
@@ -58,6 +59,18 @@ class StepReport(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("min_det", ctypes.c_double),
                 ("minres_resid", ctypes.c_double), ("minres_iters", ctypes.c_int),
                 ("halvings", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RemapOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("cg_rtol", ctypes.c_double), ("cg_max_it", ctypes.c_int)]
+
+
+class RemapReport(ctypes.Structure):
+    _fields_ = [("cg_iters", ctypes.c_int), ("solves", ctypes.c_int), ("min_det", ctypes.c_double),
+                ("status", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -120,6 +133,9 @@ def lib():
             "tmop_batch_device_bytes": (I64, [P]),
             "tmop_batch_destroy": (None, [P]),
             "tmop_set_limit_reference": (I, [P, P]),
+            "tmop_set_target_field": (I, [P, P]),
+            "tmop_set_remap_source": (I, [P, P, P, ctypes.POINTER(RemapOpts)]),
+            "tmop_remap": (I, [P, P, P, P, P, ctypes.POINTER(RemapOpts), ctypes.POINTER(RemapReport)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -204,6 +220,28 @@ def tmop_newton_step(ctx: int, x, opts: SolverOpts | None = None) -> dict:
 
 def tmop_set_limit_reference(ctx: int, x0):
     _check(lib().tmop_set_limit_reference(ctx, _ptr(x0)), "tmop_set_limit_reference")
+
+
+def tmop_set_target_field(ctx: int, eta):
+    _check(lib().tmop_set_target_field(ctx, _ptr(eta)), "tmop_set_target_field")
+
+
+def tmop_set_remap_source(ctx: int, x0, eta0, opts: RemapOpts | None = None):
+    _check(lib().tmop_set_remap_source(ctx, _ptr(x0), _ptr(eta0),
+                                       ctypes.byref(opts) if opts is not None else None),
+           "tmop_set_remap_source")
+
+
+def tmop_remap(ctx: int, x0, x1, eta0, eta1, opts: RemapOpts | None = None) -> dict:
+    """Status in the returned dict (TMOP_ERR_INVERTED is reported, not raised)."""
+    rep = RemapReport()
+    st = lib().tmop_remap(ctx, _ptr(x0), _ptr(x1), _ptr(eta0), _ptr(eta1),
+                          ctypes.byref(opts) if opts is not None else None, ctypes.byref(rep))
+    if st not in (OK, ERR_INVERTED):
+        _check(st, "tmop_remap")
+    d = rep.as_dict()
+    d["status"] = st
+    return d
 
 
 def tmop_destroy(ctx: int):

@@ -704,6 +704,8 @@ tmop_status tmop_batch_create(const tmop_batch_desc *desc, void *cuda_stream, tm
         return bfail(TMOP_ERR_UNSUPPORTED, "order must be 1..4 and nq1d order+1, order+2 (or 9 in 3D)");
     const bool mok = metric_valid(D.metric, D.dim);
     if (!mok) return bfail(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
+    if (D.target == TMOP_TARGET_DISCRETE)
+        return bfail(TMOP_ERR_UNSUPPORTED, "the discrete target needs a field per mesh: tmop_setup only");
     if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
         return bfail(TMOP_ERR_ARG, "unknown target");
     if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32 &&

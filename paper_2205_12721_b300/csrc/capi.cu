@@ -2,6 +2,7 @@
 // entry points of the hot path and the host-driven Newton / MINRES loop.
 // Every arithmetic step runs in the kernels of elem_*.cu and vec_kernels.cu;
 // this file validates arguments, owns device memory and sequences launches.
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cmath>
@@ -90,6 +91,21 @@ struct tmop_ctx {
     double lim2 = 0.0;                 // 2 / delta^2, 0 when off
     double *x0 = nullptr, *lim_cq = nullptr, *part2 = nullptr;
     bool x0_set = false;
+    // discrete target field and its remap (allocated on first use)
+    double *eta = nullptr, *eta_t = nullptr;
+    bool eta_set = false;
+    double *rsrc_x0 = nullptr, *rsrc_eta0 = nullptr;
+    bool remap_on = false;
+    tmop_remap_opts remap_opts{4, 1e-12, 200};
+    struct Remap {
+        bool ready = false;
+        double *vel = nullptr, *dm[2] = {nullptr, nullptr}, *dadv[2] = {nullptr, nullptr};
+        double *dinv[2] = {nullptr, nullptr}, *k[4] = {nullptr}, *es = nullptr, *rhs = nullptr;
+        double *r = nullptr, *z = nullptr, *pv = nullptr, *Mp = nullptr, *mind = nullptr;
+        CgState *cg = nullptr, *hcg = nullptr;   // device state, pinned host mirror
+        double *hmind = nullptr;
+        int last_its = 8;
+    } rm;
     // instrumentation
     bool prof = false;
     std::vector<ProfRec> pending;
@@ -111,6 +127,7 @@ struct tmop_ctx {
         P.metric = desc.metric;
         P.target = desc.target;
         P.h0 = desc.target_h0;
+        P.eta = eta;
         return P;
     }
 
@@ -197,6 +214,13 @@ tmop_status limit_ready(tmop_ctx *c)
     return TMOP_OK;
 }
 
+tmop_status target_ready(tmop_ctx *c)
+{
+    if (c->desc.target == TMOP_TARGET_DISCRETE && !c->eta_set)
+        return fail(TMOP_ERR_ARG, "discrete target: call tmop_set_target_field or tmop_set_remap_source");
+    return TMOP_OK;
+}
+
 // Limiting energy into scal[4] (and its gradient added into ev64 when ev).
 tmop_status limit_eg_async(tmop_ctx *c, const double *x, double *ev)
 {
@@ -212,6 +236,7 @@ tmop_status limit_eg_async(tmop_ctx *c, const double *x, double *ev)
 tmop_status energy_async(tmop_ctx *c, const double *x)
 {
     TRY(limit_ready(c));
+    TRY(target_ready(c));
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
     TRY(timed(c, TMOP_K_ENERGY, "energy kernel",
@@ -244,6 +269,7 @@ tmop_status energy_sync(tmop_ctx *c, const double *x, double *F, double *md)
 tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
 {
     TRY(limit_ready(c));
+    TRY(target_ready(c));
     const ElemParams P = c->params();
     TRY(timed(c, TMOP_K_GRADIENT, "gradient kernel",
               [&] { return launch_gradient(c->d, c->p, c->nq, P, x, c->ev64, c->arith, c->stream); }));
@@ -260,6 +286,7 @@ tmop_status gradient_async(tmop_ctx *c, const double *x, double *g)
 tmop_status energy_grad_sync(tmop_ctx *c, const double *x, double *g, double *F, double *md)
 {
     TRY(limit_ready(c));
+    TRY(target_ready(c));
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
     TRY(timed(c, TMOP_K_GRADIENT, "energy+gradient kernel", [&] {
@@ -297,6 +324,7 @@ tmop_status norm_sync(tmop_ctx *c, const double *a, double *out)
 tmop_status hsetup_async(tmop_ctx *c, const double *x)
 {
     TRY(limit_ready(c));
+    TRY(target_ready(c));
     const ElemParams P = c->params();
     TRY(timed(c, TMOP_K_HSETUP, "hessian setup kernel",
               [&] { return launch_hsetup(c->d, c->p, c->nq, P, x, c->H, c->prec, c->stream); }));
@@ -318,6 +346,139 @@ tmop_status apply_internal(tmop_ctx *c, const void *v, void *y, const int *stop,
         return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
                                c->Nx, c->d, c->ENP, y, c->vprec, stop, k, c->stream);
     }));
+    return TMOP_OK;
+}
+
+// ---------------------------------------------------------------- remap (Sec. 3.6)
+tmop_status remap_alloc(tmop_ctx *c)
+{
+    auto &R = c->rm;
+    if (R.ready) return TMOP_OK;
+    const size_t nq = (size_t)c->E * c->nqd;
+    TRY(c->alloc(&R.vel, c->ndof));
+    for (int i = 0; i < 2; ++i) {
+        TRY(c->alloc(&R.dm[i], nq));
+        TRY(c->alloc(&R.dadv[i], (size_t)c->d * nq));
+        TRY(c->alloc(&R.dinv[i], c->Nx));
+    }
+    for (int i = 0; i < 4; ++i) TRY(c->alloc(&R.k[i], c->Nx));
+    TRY(c->alloc(&R.es, c->Nx));
+    TRY(c->alloc(&R.rhs, c->Nx));
+    TRY(c->alloc(&R.r, c->Nx));
+    TRY(c->alloc(&R.z, c->Nx));
+    TRY(c->alloc(&R.pv, c->Nx));
+    TRY(c->alloc(&R.Mp, c->Nx));
+    TRY(c->alloc(&R.mind, 1));
+    TRY(c->alloc((double **)&R.cg, sizeof(CgState) / sizeof(double) + 1));
+    if (!R.hcg) CK(cudaMallocHost((void **)&R.hcg, sizeof(CgState)));
+    if (!R.hmind) CK(cudaMallocHost((void **)&R.hmind, sizeof(double)));
+    R.ready = true;
+    return TMOP_OK;
+}
+
+// Mass data, advection data and the inverse mass diagonal of x_t into set i;
+// min det A of x_t folded into rm.mind.
+tmop_status remap_setup(tmop_ctx *c, const double *x0, double t, int i, bool reset)
+{
+    auto &R = c->rm;
+    const ElemParams P = c->params();
+    const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
+    CK(launch_remap_setup(c->d, c->p, c->nq, P, x0, R.vel, t, R.dm[i], R.dadv[i], c->part, c->arith,
+                          c->stream));
+    CK(launch_min_accum(c->part, nb, R.mind, reset ? 1 : 0, c->stream));
+    CK(launch_mass_diag(c->d, c->p, c->nq, P, R.dm[i], c->ev64, c->arith, c->stream));
+    CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx, 1,
+                       c->ENP, R.rhs, TMOP_FP64, nullptr, 0, c->stream));
+    CK(launch_recip(R.rhs, c->Nx, R.dinv[i], c->stream));
+    return TMOP_OK;
+}
+
+// kout = M_i^-1 K_i u by Jacobi-CG; the host reads the stop flag once per
+// chunk of iterations (the first chunk as long as the previous solve).
+tmop_status remap_stage(tmop_ctx *c, const double *u, int i, double *kout, const tmop_remap_opts &o,
+                        int *its)
+{
+    auto &R = c->rm;
+    const ElemParams P = c->params();
+    const int nb = reduce_blocks(c->Nx);
+    CK(launch_adv_apply(c->d, c->p, c->nq, P, u, R.dadv[i], c->ev64, c->arith, c->stream));
+    CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx, 1,
+                       c->ENP, R.rhs, TMOP_FP64, nullptr, 0, c->stream));
+    CK(launch_cg_init(R.rhs, R.dinv[i], c->Nx, kout, R.r, R.z, R.pv, c->part, nb, o.cg_rtol, R.cg,
+                      c->stream));
+    const int *stop = &R.cg->stop;
+    int k = 0, chunk = std::max(4, R.last_its);
+    while (true) {
+        const int kend = std::min(o.cg_max_it, k + chunk);
+        for (int kk = k + 1; kk <= kend; ++kk) {
+            CK(launch_mass_apply(c->d, c->p, c->nq, P, R.pv, R.dm[i], c->ev64, stop, kk, c->arith,
+                                 c->stream));
+            CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx,
+                               1, c->ENP, R.Mp, TMOP_FP64, stop, kk, c->stream));
+            CK(launch_cg_iter_scalars(R.pv, R.Mp, kout, R.r, R.z, R.dinv[i], c->Nx, c->part, nb, R.cg,
+                                      kk, o.cg_max_it, c->stream));
+        }
+        CK(cudaMemcpyAsync(R.hcg, R.cg, sizeof(CgState), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (R.hcg->stop <= kend || kend >= o.cg_max_it) break;
+        k = kend;
+        chunk = 4;
+    }
+    *its = R.hcg->its;
+    R.last_its = std::max(1, R.hcg->its);
+    return TMOP_OK;
+}
+
+// eta1 = eta0 advected from x0 to x1: RK4 with o.steps uniform pseudo-time
+// steps; stage times (n + c_s) dt with c = 0, 1/2, 1/2, 1; the operators at
+// (n+1) dt serve the last stage of step n and the first of step n+1.
+tmop_status remap_run(tmop_ctx *c, const double *x0, const double *x1, const double *eta0,
+                      double *eta1, const tmop_remap_opts &o, tmop_remap_report *rep)
+{
+    tmop_remap_report r{0, 0, INFINITY, TMOP_OK};
+    if (o.steps < 1 || o.cg_max_it < 1 || !(o.cg_rtol >= 0.0))
+        return fail(TMOP_ERR_ARG, "remap: steps >= 1, cg_max_it >= 1, cg_rtol >= 0 required");
+    TRY(remap_alloc(c));
+    auto &R = c->rm;
+    CK(launch_trial(x1, x0, 1.0, c->ndof, R.vel, c->stream));          // v = x1 - x0
+    if (eta1 != eta0)
+        CK(cudaMemcpyAsync(eta1, eta0, sizeof(double) * c->Nx, cudaMemcpyDeviceToDevice, c->stream));
+    const double dt = 1.0 / o.steps;
+    int its = 0;
+    TRY(remap_setup(c, x0, 0.0, 0, true));
+    for (int n = 0; n < o.steps; ++n) {
+        TRY(remap_stage(c, eta1, 0, R.k[0], o, &its));
+        r.cg_iters += its;
+        TRY(remap_setup(c, x0, (n + 0.5) * dt, 1, false));
+        CK(launch_axpy(eta1, R.k[0], 0.5 * dt, c->Nx, R.es, c->stream));
+        TRY(remap_stage(c, R.es, 1, R.k[1], o, &its));
+        r.cg_iters += its;
+        CK(launch_axpy(eta1, R.k[1], 0.5 * dt, c->Nx, R.es, c->stream));
+        TRY(remap_stage(c, R.es, 1, R.k[2], o, &its));
+        r.cg_iters += its;
+        TRY(remap_setup(c, x0, (n + 1.0) * dt, 0, false));
+        CK(launch_axpy(eta1, R.k[2], dt, c->Nx, R.es, c->stream));
+        TRY(remap_stage(c, R.es, 0, R.k[3], o, &its));
+        r.cg_iters += its;
+        CK(launch_rk4_combine(eta1, R.k[0], R.k[1], R.k[2], R.k[3], dt, c->Nx, c->stream));
+        r.solves += 4;
+    }
+    CK(cudaMemcpyAsync(R.hmind, R.mind, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    r.min_det = *R.hmind;
+    if (!(r.min_det > 0.0) && c->E > 0) {
+        r.status = TMOP_ERR_INVERTED;
+        if (rep) *rep = r;
+        return fail(TMOP_ERR_INVERTED, "remap: det(A) <= 0 on an intermediate mesh");
+    }
+    if (rep) *rep = r;
+    return TMOP_OK;
+}
+
+tmop_status eta_alloc(tmop_ctx *c)
+{
+    if (!c->eta) TRY(c->alloc(&c->eta, c->Nx));
+    if (!c->eta_t) TRY(c->alloc(&c->eta_t, c->Nx));
     return TMOP_OK;
 }
 
@@ -420,6 +581,8 @@ void tmop_destroy(tmop_ctx *ctx)
     for (void *q : ctx->allocs) cudaFree(q);
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
     if (ctx->hst) cudaFreeHost(ctx->hst);
+    if (ctx->rm.hcg) cudaFreeHost(ctx->rm.hcg);
+    if (ctx->rm.hmind) cudaFreeHost(ctx->rm.hmind);
     delete ctx;
 }
 
@@ -435,9 +598,10 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
         return fail(TMOP_ERR_UNSUPPORTED, "nq1d must be order+1, order+2 (or 9 in 3D)");
     if (D.num_elems < 0 || D.num_nodes <= 0) return fail(TMOP_ERR_ARG, "bad mesh sizes");
     if (!metric_ok(D.metric, D.dim)) return fail(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
-    if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
+    if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD &&
+        D.target != TMOP_TARGET_DISCRETE)
         return fail(TMOP_ERR_ARG, "unknown target");
-    if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))
+    if (D.target != TMOP_TARGET_IDENTITY && !(D.target_h0 > 0.0))
         return fail(TMOP_ERR_ARG, "target_h0 must be > 0");
     if (D.limit_delta < 0.0 || D.limit_delta != D.limit_delta)
         return fail(TMOP_ERR_ARG, "limit_delta must be >= 0");
@@ -635,7 +799,12 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         return st;
     };
     double F0 = 0, md0 = 0;
-    tmop_status st = energy_grad_sync(c, x, c->g, &F0, &md0);
+    tmop_status st = TMOP_OK;
+    if (c->remap_on) {      // discrete target: eta follows the positions (Sec. 3.6)
+        st = remap_run(c, c->rsrc_x0, x, c->rsrc_eta0, c->eta, c->remap_opts, nullptr);
+        if (st != TMOP_OK) return finish(st);
+    }
+    st = energy_grad_sync(c, x, c->g, &F0, &md0);
     r.energy = F0;
     r.min_det = md0;
     if (st != TMOP_OK) return finish(st);
@@ -665,14 +834,25 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
     for (int h = 0; h <= o.ls_max_halvings; ++h, alpha *= 0.5) {
         cudaError_t e = launch_trial(x, c->dx, alpha, c->ndof, c->xt, c->stream);
         if (e != cudaSuccess) return finish(cuda_fail(e, "trial"));
+        // with the remap, the trial is evaluated with eta remapped to it; the
+        // field of the accepted trial stays in c->eta
+        bool swapped = false;
+        auto restore = [&] { if (swapped) std::swap(c->eta, c->eta_t); swapped = false; };
+        if (c->remap_on) {
+            st = remap_run(c, c->rsrc_x0, c->xt, c->rsrc_eta0, c->eta_t, c->remap_opts, nullptr);
+            if (st == TMOP_ERR_INVERTED) continue;        // x_t inverted on the way
+            if (st != TMOP_OK) return finish(st);
+            std::swap(c->eta, c->eta_t);
+            swapped = true;
+        }
         double F1 = 0, md1 = 0;
         st = energy_grad_sync(c, c->xt, c->g, &F1, &md1);
-        if (st == TMOP_ERR_INVERTED) continue;            // det A(x+) > 0 required
-        if (st != TMOP_OK) return finish(st);
-        if (!(F1 < o.ls_factor * F0)) continue;           // energy test
+        if (st == TMOP_ERR_INVERTED) { restore(); continue; }   // det A(x+) > 0 required
+        if (st != TMOP_OK) { restore(); return finish(st); }
+        if (!(F1 < o.ls_factor * F0)) { restore(); continue; }  // energy test
         double g1 = 0;
-        if ((st = norm_sync(c, c->g, &g1)) != TMOP_OK) return finish(st);
-        if (!(g1 < o.ls_factor * g0)) continue;           // gradient test
+        if ((st = norm_sync(c, c->g, &g1)) != TMOP_OK) { restore(); return finish(st); }
+        if (!(g1 < o.ls_factor * g0)) { restore(); continue; }  // gradient test
         e = cudaMemcpyAsync(x, c->xt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, c->stream);
         if (e != cudaSuccess) return finish(cuda_fail(e, "accept"));
         e = cudaStreamSynchronize(c->stream);
@@ -695,6 +875,53 @@ tmop_status tmop_set_limit_reference(tmop_ctx *ctx, const double *x0)
     CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->x0_set = true;
     return TMOP_OK;
+}
+
+tmop_status tmop_set_target_field(tmop_ctx *ctx, const double *eta)
+{
+    if (!ctx || !eta) return fail(TMOP_ERR_ARG, "NULL argument");
+    if (ctx->desc.target != TMOP_TARGET_DISCRETE) return fail(TMOP_ERR_ARG, "context target is not DISCRETE");
+    TRY(eta_alloc(ctx));
+    CK(cudaMemcpyAsync(ctx->eta, eta, sizeof(double) * ctx->Nx, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->eta_set = true;
+    return TMOP_OK;
+}
+
+tmop_status tmop_set_remap_source(tmop_ctx *ctx, const double *x0, const double *eta0,
+                                  const tmop_remap_opts *opts)
+{
+    if (!ctx) return fail(TMOP_ERR_ARG, "NULL context");
+    if (ctx->desc.target != TMOP_TARGET_DISCRETE) return fail(TMOP_ERR_ARG, "context target is not DISCRETE");
+    if (!eta0) {
+        ctx->remap_on = false;
+        return TMOP_OK;
+    }
+    if (!x0) return fail(TMOP_ERR_ARG, "x0 is NULL");
+    tmop_remap_opts o{4, 1e-12, 200};
+    if (opts) o = *opts;
+    if (o.steps < 1 || o.cg_max_it < 1 || !(o.cg_rtol >= 0.0))
+        return fail(TMOP_ERR_ARG, "remap: steps >= 1, cg_max_it >= 1, cg_rtol >= 0 required");
+    TRY(eta_alloc(ctx));
+    if (!ctx->rsrc_x0) TRY(ctx->alloc(&ctx->rsrc_x0, ctx->ndof));
+    if (!ctx->rsrc_eta0) TRY(ctx->alloc(&ctx->rsrc_eta0, ctx->Nx));
+    CK(cudaMemcpyAsync(ctx->rsrc_x0, x0, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->rsrc_eta0, eta0, sizeof(double) * ctx->Nx, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->eta, eta0, sizeof(double) * ctx->Nx, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->remap_opts = o;
+    ctx->remap_on = true;
+    ctx->eta_set = true;
+    return TMOP_OK;
+}
+
+tmop_status tmop_remap(tmop_ctx *ctx, const double *x0, const double *x1, const double *eta0,
+                       double *eta1, const tmop_remap_opts *opts, tmop_remap_report *rep)
+{
+    if (!ctx || !x0 || !x1 || !eta0 || !eta1) return fail(TMOP_ERR_ARG, "NULL argument");
+    tmop_remap_opts o{4, 1e-12, 200};
+    if (opts) o = *opts;
+    tmop_status st = remap_run(ctx, x0, x1, eta0, eta1, o, rep);
+    if (st == TMOP_OK) g_last_error.clear();
+    return st;
 }
 
 tmop_status tmop_profile_enable(tmop_ctx *ctx, int on)

@@ -79,6 +79,62 @@ __device__ __forceinline__ void forward_component(const ElemParams &P, ElemCtx<C
         fwd2<C, R>(c.B, c.G, c.su, c.s1, A0, A0 + C::NQD, xv, c.tx, c.ty, c.valid);
 }
 
+// Forward pass of the element geometry: the Jacobian rows of x into sA;
+// the physical point coordinates into sX for the size target, or the
+// interpolated target field eta into sX[0..NQD) for the discrete target
+// (its derivative outputs land in sA rows that the x components overwrite).
+template <class C, class R>
+__device__ __forceinline__ void forward_geometry(const ElemParams &P, ElemCtx<C, R> &c,
+                                                 const double *__restrict__ x)
+{
+    if (P.target == TGT_DISCRETE) {
+        if (c.valid)
+            for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = R(P.eta[c.smap[i]]);
+        __syncthreads();
+        if (C::D == 3)
+            fwd3<C, R>(c.B, c.G, c.su, c.s1, c.s2, c.sA, c.sA + C::NQD, c.sA + 2 * C::NQD, c.sX,
+                       c.tx, c.ty, c.valid);
+        else
+            fwd2<C, R>(c.B, c.G, c.su, c.s1, c.sA, c.sA + C::NQD, c.sX, c.tx, c.ty, c.valid);
+    }
+    const bool want_x = P.target == TGT_SIZE;
+    for (int a = 0; a < C::D; ++a) forward_component<C, R, double>(P, c, x, a, want_x);
+}
+
+// Values at the points of component a of an L-vector u (minus u0 when given):
+// the B-only path of the forward contractions, into out[q]; sA rows 0..D-1
+// take the discarded derivatives.
+template <class C, class R, class RIN>
+__device__ __forceinline__ void values_at_points(const ElemParams &P, ElemCtx<C, R> &c,
+                                                 const RIN *__restrict__ u, const RIN *__restrict__ u0,
+                                                 int a, R *out)
+{
+    if (c.valid)
+        for (int i = c.t; i < C::NP; i += C::TPE) {
+            const int64_t j = a * P.Nx + c.smap[i];
+            c.su[i] = R(u0 ? (double)u[j] - (double)u0[j] : (double)u[j]);
+        }
+    __syncthreads();
+    if (C::D == 3)
+        fwd3<C, R>(c.B, c.G, c.su, c.s1, c.s2, c.sA, c.sA + C::NQD, c.sA + 2 * C::NQD, out, c.tx, c.ty,
+                   c.valid);
+    else
+        fwd2<C, R>(c.B, c.G, c.su, c.s1, c.sA, c.sA + C::NQD, out, c.tx, c.ty, c.valid);
+}
+
+// su_i = sum_q f(q) w_i(chi_q) for all element nodes (zeroes su first)
+template <class C, class R>
+__device__ __forceinline__ void values_transpose(ElemCtx<C, R> &c, const R *f)
+{
+    if (c.valid)
+        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = R(0.0);
+    __syncthreads();
+    if (C::D == 3)
+        bwd3_tab<C, R>(c.B, c.B, c.B, f, c.s1, c.s2, c.su, c.tx, c.ty, c.valid);
+    else
+        bwd2_tab<C, R>(c.B, c.B, f, c.s1, c.su, c.tx, c.ty, c.valid);
+}
+
 // Transposed contractions of sA[(a*D + b)*NQD + q] (b = derivative
 // direction) and store of the element vector component a.
 template <class C, class R, class ROUT>
@@ -118,6 +174,7 @@ __device__ __forceinline__ double point_weight(const R *w, int tx, int ty, int q
 template <class C, class R>
 __device__ __forceinline__ double point_target(const ElemParams &P, const R *sX, int q)
 {
+    if (P.target == TGT_DISCRETE) return discrete_scale<C::D>(P.h0, to_db(sX[q]));
     double xq[3] = {0, 0, 0};
     if (P.target == TGT_SIZE)
 #pragma unroll
@@ -162,8 +219,7 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
     prologue<C, RS>(P, tile, smem, c);
-    const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
+    forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
@@ -178,7 +234,7 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
         for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
-        const double detA = tau * wd;
+        const double detA = ws > 0.0 ? tau * wd : -INFINITY;   // no target: inverted
         emin = fmin(emin, detA);
         if (detA > 0.0) {
             Inv v;
@@ -206,8 +262,7 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
     prologue<C, RS>(P, tile, smem, c);
-    const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
+    forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
@@ -222,8 +277,8 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
         for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
-        emin = fmin(emin, tau * wd);
-        if (!(tau > 0.0)) {                               // inverted points contribute 0
+        emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+        if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points contribute 0
 #pragma unroll
             for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0);
             return;
@@ -262,8 +317,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RS> c;
     prologue<C, RS>(P, tile, smem, c);
-    const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, RS, double>(P, c, x, a, want_x);
+    forward_geometry<C, RS>(P, c, x);
 
     RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
@@ -278,7 +332,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
         invariants<C::D>(T, I1, tau, I2, Cf);
-        if (!(tau > 0.0)) {                               // inverted points store 0
+        if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points store 0
 #pragma unroll
             for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0);
             return;

@@ -12,39 +12,6 @@ namespace tmop {
 
 namespace {
 
-// values at the points of element field u_a (the B-only path of the forward
-// contractions), into out[q]; dA is scratch for the discarded derivatives
-template <class C, class R, class RIN>
-__device__ __forceinline__ void values_at_points(const ElemParams &P, ElemCtx<C, R> &c,
-                                                 const RIN *__restrict__ u, const RIN *__restrict__ u0,
-                                                 int a, R *out)
-{
-    if (c.valid)
-        for (int i = c.t; i < C::NP; i += C::TPE) {
-            const int64_t j = a * P.Nx + c.smap[i];
-            c.su[i] = R(u0 ? (double)u[j] - (double)u0[j] : (double)u[j]);
-        }
-    __syncthreads();
-    if (C::D == 3)
-        fwd3<C, R>(c.B, c.G, c.su, c.s1, c.s2, c.sA, c.sA + C::NQD, c.sA + 2 * C::NQD, out, c.tx, c.ty,
-                   c.valid);
-    else
-        fwd2<C, R>(c.B, c.G, c.su, c.s1, c.sA, c.sA + C::NQD, out, c.tx, c.ty, c.valid);
-}
-
-// out_i += sum_q f(q) w_i(chi_q) for all element nodes (zeroes su first)
-template <class C, class R>
-__device__ __forceinline__ void values_transpose(ElemCtx<C, R> &c, const R *f)
-{
-    if (c.valid)
-        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = R(0.0);
-    __syncthreads();
-    if (C::D == 3)
-        bwd3_tab<C, R>(c.B, c.B, c.B, f, c.s1, c.s2, c.su, c.tx, c.ty, c.valid);
-    else
-        bwd2_tab<C, R>(c.B, c.B, f, c.s1, c.su, c.tx, c.ty, c.valid);
-}
-
 // Energy partials (2 per CTA: sum, +inf) and, if ev != nullptr, the gradient
 // added into the element vector.  c_q = w_q det W(x_q).
 template <class C, class RS>
@@ -62,6 +29,7 @@ k_limit_eg(ElemParams P, const double *__restrict__ x, const double *__restrict_
     for (int a = 0; a < C::D; ++a) values_at_points<C, RS, double>(P, c, x, x0, a, dq + a * C::NQD);
     if (P.target == TGT_SIZE)
         for (int a = 0; a < C::D; ++a) values_at_points<C, RS, double>(P, c, x, nullptr, a, xq + a * C::NQD);
+    if (P.target == TGT_DISCRETE) values_at_points<C, RS, double>(P, c, P.eta, nullptr, 0, xq);
     __syncthreads();
     double esum = 0.0;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
@@ -69,7 +37,13 @@ k_limit_eg(ElemParams P, const double *__restrict__ x, const double *__restrict_
         if (P.target == TGT_SIZE)
 #pragma unroll
             for (int k = 0; k < C::D; ++k) xp[k] = to_db(xq[k * C::NQD + q]);
-        const double ws = target_scale<C::D>(P.target, P.h0, xp);
+        double ws = target_scale<C::D>(P.target, P.h0, xp);
+        if (P.target == TGT_DISCRETE) ws = discrete_scale<C::D>(P.h0, to_db(xq[q]));
+        if (!(ws > 0.0)) {                            // no target: no contribution
+#pragma unroll
+            for (int a = 0; a < C::D; ++a) dq[a * C::NQD + q] = RS(0.0);
+            return;
+        }
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
@@ -105,13 +79,19 @@ k_limit_setup(ElemParams P, const double *__restrict__ x, double lim2, double *_
     prologue<C, df>(P, blockIdx.x, smem, c);
     if (P.target == TGT_SIZE)
         for (int a = 0; a < C::D; ++a) values_at_points<C, df, double>(P, c, x, nullptr, a, c.sX + a * C::NQD);
+    if (P.target == TGT_DISCRETE) values_at_points<C, df, double>(P, c, P.eta, nullptr, 0, c.sX);
     __syncthreads();
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double xp[3] = {0, 0, 0};
         if (P.target == TGT_SIZE)
 #pragma unroll
             for (int k = 0; k < C::D; ++k) xp[k] = to_db(c.sX[k * C::NQD + q]);
-        const double ws = target_scale<C::D>(P.target, P.h0, xp);
+        double ws = target_scale<C::D>(P.target, P.h0, xp);
+        if (P.target == TGT_DISCRETE) ws = discrete_scale<C::D>(P.h0, to_db(c.sX[q]));
+        if (!(ws > 0.0)) {
+            cq_out[c.e * C::NQD + q] = 0.0;
+            return;
+        }
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;

@@ -65,6 +65,8 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
         return set_error(TMOP_ERR_UNSUPPORTED, "order must be 1..4 and nq1d order+1, order+2 (or 9 in 3D)");
     const bool metric_ok = metric_valid(D.metric, D.dim);
     if (!metric_ok) return set_error(TMOP_ERR_UNSUPPORTED, "metric not defined for this dim");
+    if (D.target == TMOP_TARGET_DISCRETE)
+        return set_error(TMOP_ERR_UNSUPPORTED, "the discrete target needs a field per mesh: tmop_setup only");
     if (D.target != TMOP_TARGET_IDENTITY && D.target != TMOP_TARGET_SIZE_FIELD)
         return set_error(TMOP_ERR_ARG, "unknown target");
     if (D.target == TMOP_TARGET_SIZE_FIELD && !(D.target_h0 > 0.0))

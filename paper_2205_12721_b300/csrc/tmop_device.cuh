@@ -31,7 +31,7 @@ __host__ __device__ inline bool metric_uses_I2(int m, int d)
 {
     return d == 3 && (m == MET_302 || m == MET_7 || m == MET_9);
 }
-enum { TGT_IDENTITY = 0, TGT_SIZE = 1 };
+enum { TGT_IDENTITY = 0, TGT_SIZE = 1, TGT_DISCRETE = 2 };
 
 template <int D_, int P_, int Q_>
 struct Cfg {
@@ -61,6 +61,7 @@ struct ElemParams {
     const df *__restrict__ tabw;       // same, double-float
     int metric, target;
     double h0;
+    const double *__restrict__ eta = nullptr;   // nodal field of the discrete target (Nx)
 };
 
 // ---- batched launches: one grid over the element tiles of many meshes ----
@@ -595,6 +596,15 @@ __device__ __forceinline__ double target_scale(int target, double h0, const doub
     for (int k = 0; k < D; ++k) s *= sin(twopi * xq[k]);
     s += 1.0;
     return h0 * (D == 3 ? cbrt(s) : sqrt(s));
+}
+
+// Target scale of the discrete target, w = h0 eta_q^(1/D); NaN when
+// eta_q <= 0 (no target: the callers treat the point as inverted).
+template <int D>
+__device__ __forceinline__ double discrete_scale(double h0, double eta_q)
+{
+    if (!(eta_q > 0.0)) return __longlong_as_double(0x7ff8000000000000LL);
+    return h0 * (D == 3 ? cbrt(eta_q) : sqrt(eta_q));
 }
 
 // Table of the compute type R.

@@ -57,6 +57,18 @@ cudaError_t launch_limit_apply(int d, int p, int q, const ElemParams &P, const v
 cudaError_t launch_limit_diag(int d, int p, int q, const ElemParams &P, const double *cq, void *ev,
                               int prec, cudaStream_t s);
 
+// Advection remap of the discrete target field (remap.cu), arith as above.
+cudaError_t launch_remap_setup(int d, int p, int q, const ElemParams &P, const double *x0,
+                               const double *vel, double t, double *dm, double *dadv, double *part,
+                               int arith, cudaStream_t s);
+cudaError_t launch_mass_apply(int d, int p, int q, const ElemParams &P, const double *u,
+                              const double *dm, double *ev, const int *stop, int kk, int arith,
+                              cudaStream_t s);
+cudaError_t launch_mass_diag(int d, int p, int q, const ElemParams &P, const double *dm, double *ev,
+                             int arith, cudaStream_t s);
+cudaError_t launch_adv_apply(int d, int p, int q, const ElemParams &P, const double *u,
+                             const double *dadv, double *ev, int arith, cudaStream_t s);
+
 // Host tables: Gauss-Legendre rule on [0,1], GLL nodes, Lagrange B/G.
 void host_gauss_legendre(int n, double *x, double *w);
 void host_gll_nodes(int n, double *x);
@@ -69,6 +81,13 @@ struct MinresState {
     int breakdown;
     int iters;
     int pad;
+};
+
+// CG scalar state of one remap mass solve, kept on the device.
+struct CgState {
+    int stop;        // iterations done when the solve ended (INT_MAX while running)
+    int its;
+    double rz, rz_stop, alpha, beta;
 };
 
 // Vector / reduction launchers (vec_kernels.cu).
@@ -103,6 +122,21 @@ cudaError_t launch_fin_beta(const double *part, int nb, MinresState *st, int k, 
 cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *wnew, double *dx,
                                  const void *ynew, const MinresState *st, int prec, int64_t n,
                                  int k, cudaStream_t s);
+
+// Remap CG and RK4 vector kernels (vec_kernels.cu).  One CG iteration kk
+// (1-based) is the mass action (remap.cu) followed by launch_cg_iter_scalars.
+cudaError_t launch_cg_init(const double *b, const double *dinv, int64_t n, double *k, double *r,
+                           double *z, double *p, double *part, int nb, double rtol, CgState *st,
+                           cudaStream_t s);
+cudaError_t launch_cg_iter_scalars(const double *p, const double *Mp, double *k, double *r,
+                                   double *z, const double *dinv, int64_t n, double *part, int nb,
+                                   CgState *st, int kk, int max_it, cudaStream_t s);
+cudaError_t launch_axpy(const double *u, const double *k, double c, int64_t n, double *out,
+                        cudaStream_t s);
+cudaError_t launch_rk4_combine(double *u, const double *k1, const double *k2, const double *k3,
+                               const double *k4, double dt, int64_t n, cudaStream_t s);
+cudaError_t launch_recip(const double *d, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_min_accum(const double *part, int64_t nb, double *acc, int reset, cudaStream_t s);
 
 // Global launch counter (instrumentation).
 void count_launch(int n = 1);

@@ -256,6 +256,170 @@ inline unsigned grid_for(int64_t n)
 
 }  // namespace
 
+// ---------------------------------------------------------------- remap CG / RK4
+// Jacobi-preconditioned CG for the mass solves of the advection remap
+// (Sec. 3.6).  The scalars live in CgState on the device; iteration kk
+// (1-based) runs only while st->stop >= kk, so a fixed launch sequence
+// stops doing work once the solve has converged.
+namespace {
+
+// k = 0, r = b, z = dinv r, p = z; partial r.z
+__global__ void k_cg_init(const double *__restrict__ b, const double *__restrict__ dinv, int64_t n,
+                          double *__restrict__ k, double *__restrict__ r, double *__restrict__ z,
+                          double *__restrict__ p, double *__restrict__ part)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i], zi = dinv[i] * bi;
+        k[i] = 0.0;
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        s += bi * zi;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_cg_start(const double *__restrict__ part, int nb, double rtol, CgState *st)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        st->rz = s;
+        st->rz_stop = rtol * rtol * s;
+        st->stop = (s > st->rz_stop && s > 0.0) ? INT_MAX : 0;
+        st->its = 0;
+        st->alpha = st->beta = 0.0;
+    }
+}
+
+// partial p.Mp
+__global__ void k_cg_dot(const double *__restrict__ p, const double *__restrict__ q, int64_t n,
+                         double *__restrict__ part, const CgState *__restrict__ st, int kk)
+{
+    if (st->stop < kk) return;
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += p[i] * q[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// alpha = r.z / p.Mp; a non-positive p.Mp (mass operator of an inverted
+// mesh) ends the solve before the update
+__global__ void k_cg_alpha(const double *__restrict__ part, int nb, CgState *st, int kk)
+{
+    if (st->stop < kk) return;
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        if (s > 0.0) {
+            st->alpha = st->rz / s;
+        } else {
+            st->alpha = 0.0;
+            st->stop = kk - 1;
+        }
+    }
+}
+
+// k += alpha p, r -= alpha Mp, z = dinv r; partial r.z
+__global__ void k_cg_update(double *__restrict__ k, double *__restrict__ r, double *__restrict__ z,
+                            const double *__restrict__ p, const double *__restrict__ q,
+                            const double *__restrict__ dinv, int64_t n, double *__restrict__ part,
+                            const CgState *__restrict__ st, int kk)
+{
+    if (st->stop < kk) return;
+    __shared__ double sh[VT / 32];
+    const double a = st->alpha;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        k[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        s += ri * zi;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// new r.z, beta, convergence (or the iteration cap) -> stop = kk
+__global__ void k_cg_beta(const double *__restrict__ part, int nb, CgState *st, int kk, int max_it)
+{
+    if (st->stop < kk) return;
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        st->beta = s / st->rz;
+        st->rz = s;
+        st->its = kk;
+        if (!(s > st->rz_stop) || !(s > 0.0) || kk >= max_it) st->stop = kk;
+    }
+}
+
+// p = z + beta p
+__global__ void k_cg_dir(double *__restrict__ p, const double *__restrict__ z, int64_t n,
+                         const CgState *__restrict__ st, int kk)
+{
+    if (st->stop <= kk) return;         // no further iteration uses p
+    const double b = st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
+// out = u + c k
+__global__ void k_axpy(const double *__restrict__ u, const double *__restrict__ k, double c, int64_t n,
+                       double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = u[i] + c * k[i];
+}
+
+// u += dt/6 (k1 + 2 k2 + 2 k3 + k4)
+__global__ void k_rk4_combine(double *__restrict__ u, const double *__restrict__ k1,
+                              const double *__restrict__ k2, const double *__restrict__ k3,
+                              const double *__restrict__ k4, double dt, int64_t n)
+{
+    const double h = dt / 6.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+__global__ void k_recip(const double *__restrict__ d, int64_t n, double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = 1.0 / d[i];
+}
+
+// acc = min(acc, min over the (sum, min) pairs of part); reset: acc = min over part
+__global__ void k_min_accum(const double *__restrict__ part, int64_t nb, double *acc, int reset)
+{
+    __shared__ double shm[VT / 32];
+    double m = INFINITY;
+    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) m = fmin(m, part[2 * i + 1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) shm[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, shm[i]);
+        *acc = reset ? m : fmin(*acc, m);
+    }
+}
+
+}  // namespace
+
 int reduce_blocks(int64_t n) { return (int)grid_for(n); }
 
 cudaError_t launch_assemble(const void *ev, int ev_prec, const int32_t *ptr, const int32_t *idx,
@@ -421,6 +585,62 @@ cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *
         k_minres_update<double><<<grid_for(n), VT, 0, s>>>((double *)v, (const double *)w1,
                                                           (const double *)w2, (double *)wnew, dx,
                                                           (const double *)ynew, st, n, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(const double *b, const double *dinv, int64_t n, double *k, double *r,
+                           double *z, double *p, double *part, int nb, double rtol, CgState *st,
+                           cudaStream_t s)
+{
+    k_cg_init<<<nb, VT, 0, s>>>(b, dinv, n, k, r, z, p, part);
+    k_cg_start<<<1, VT, 0, s>>>(part, nb, rtol, st);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_iter_scalars(const double *p, const double *Mp, double *k, double *r,
+                                   double *z, const double *dinv, int64_t n, double *part, int nb,
+                                   CgState *st, int kk, int max_it, cudaStream_t s)
+{
+    k_cg_dot<<<nb, VT, 0, s>>>(p, Mp, n, part, st, kk);
+    k_cg_alpha<<<1, VT, 0, s>>>(part, nb, st, kk);
+    k_cg_update<<<nb, VT, 0, s>>>(k, r, z, p, Mp, dinv, n, part, st, kk);
+    k_cg_beta<<<1, VT, 0, s>>>(part, nb, st, kk, max_it);
+    k_cg_dir<<<nb, VT, 0, s>>>(const_cast<double *>(p), z, n, st, kk);
+    count_launch(5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(const double *u, const double *k, double c, int64_t n, double *out,
+                        cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_axpy<<<grid_for(n), VT, 0, s>>>(u, k, c, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rk4_combine(double *u, const double *k1, const double *k2, const double *k3,
+                               const double *k4, double dt, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_rk4_combine<<<grid_for(n), VT, 0, s>>>(u, k1, k2, k3, k4, dt, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recip(const double *d, int64_t n, double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_recip<<<grid_for(n), VT, 0, s>>>(d, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_min_accum(const double *part, int64_t nb, double *acc, int reset, cudaStream_t s)
+{
+    k_min_accum<<<1, VT, 0, s>>>(part, nb, acc, reset);
     count_launch();
     return cudaGetLastError();
 }

@@ -39,6 +39,28 @@ class TmopMesh:
         if limit_delta > 0.0 and x0 is not None:
             self.set_limit_reference(x0)
 
+    def _dev64(self, a):
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+        return t.to(self.device, torch.float64).contiguous()
+
+    def set_target_field(self, eta):
+        """Nodal field eta of the discrete target W = h0 eta(x_q)^(1/d) I."""
+        self._eta = self._dev64(eta)
+        capi.tmop_set_target_field(self.ctx, self._eta)
+
+    def set_remap_source(self, x0, eta0, steps=4, cg_rtol=1e-12, cg_max_it=200):
+        """eta0 on positions x0: Newton remaps it to every new position."""
+        self._rx0, self._reta0 = self._dev64(x0), self._dev64(eta0)
+        capi.tmop_set_remap_source(self.ctx, self._rx0, self._reta0,
+                                   capi.RemapOpts(steps, cg_rtol, cg_max_it))
+
+    def remap(self, x0, x1, eta0, steps=4, cg_rtol=1e-12, cg_max_it=200):
+        """(eta1 tensor, report dict): eta0 advected from positions x0 to x1."""
+        x0, x1, eta0 = self._dev64(x0), self._dev64(x1), self._dev64(eta0)
+        eta1 = torch.empty_like(eta0)
+        rep = capi.tmop_remap(self.ctx, x0, x1, eta0, eta1, capi.RemapOpts(steps, cg_rtol, cg_max_it))
+        return eta1, rep
+
     def set_limit_reference(self, x0):
         """Reference positions of the limiting term |x - x0|^2 / delta^2."""
         x0d = x0 if isinstance(x0, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x0))
