@@ -360,7 +360,11 @@ int64_t tmop_launch_count(void);
 
 /* Kernel classes for per-class device timing. */
 enum { TMOP_K_ENERGY = 0, TMOP_K_GRADIENT = 1, TMOP_K_HSETUP = 2, TMOP_K_APPLY = 3,
-       TMOP_K_DIAG = 4, TMOP_K_ASSEMBLE = 5, TMOP_K_VECTOR = 6, TMOP_K_NCLASS = 7 };
+       TMOP_K_DIAG = 4, TMOP_K_ASSEMBLE = 5, TMOP_K_VECTOR = 6,
+       TMOP_K_REMAP_SETUP = 7,   /* remap operator data at x_t (+ mass diagonal) */
+       TMOP_K_MASS = 8,          /* remap mass action (element kernel) */
+       TMOP_K_ADVECT = 9,        /* remap advection action (element kernel) */
+       TMOP_K_NCLASS = 10 };
 
 /* Enable (1) or disable (0) CUDA-event timing of every element kernel
  * launch on the context's stream, and reset the accumulated figures. */

@@ -21,6 +21,7 @@ METRIC_7, METRIC_9 = 7, 9
 TARGET_IDENTITY, TARGET_SIZE_FIELD, TARGET_DISCRETE = 0, 1, 2
 FP64, FP32, FP64_NATIVE = 0, 1, 2
 K_ENERGY, K_GRADIENT, K_HSETUP, K_APPLY, K_DIAG, K_ASSEMBLE, K_VECTOR = range(7)
+K_REMAP_SETUP, K_MASS, K_ADVECT = 7, 8, 9
 
 # names declared in include/tmop.h (checked by the test-suite)
 EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",

@@ -131,18 +131,23 @@ __global__ void b_assemble(const BMesh *M, const int2 *tiles, int ev_role, int o
     RO *out = rp<RO>(bm, out_role);
     const int64_t ENP = bm.P.E * NP;
     const int b = bm.csr_ptr[n], e = bm.csr_ptr[n + 1];
-    double s[3] = {0.0, 0.0, 0.0};
+    typename AsmAcc<RI>::T s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) asm_zero(s[a]);
     for (int j = b; j < e; ++j) {
         const int64_t t = bm.csr_idx[j];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a < D) s[a] += (double)ev[a * ENP + t];
+            if (a < D) asm_add(s[a], ev[a * ENP + t]);
+        if (((j - b) & 7) == 7)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= D) break;
         const int64_t dof = a * Nx + n;
-        out[dof] = (RO)((bm.fixed && bm.fixed[dof]) ? ((mode == 2) ? 1.0 : 0.0) : s[a]);
+        out[dof] = (bm.fixed && bm.fixed[dof]) ? RO((mode == 2) ? 1.0 : 0.0) : asm_out<RO>(s[a]);
     }
 }
 

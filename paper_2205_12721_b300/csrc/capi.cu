@@ -383,8 +383,10 @@ tmop_status remap_setup(tmop_ctx *c, const double *x0, double t, int i, bool res
     auto &R = c->rm;
     const ElemParams P = c->params();
     const int64_t nb = elem_blocks(c->d, c->p, c->nq, c->E);
-    CK(launch_remap_setup(c->d, c->p, c->nq, P, x0, R.vel, t, R.dm[i], R.dadv[i], c->part, c->arith,
-                          c->stream));
+    TRY(timed(c, TMOP_K_REMAP_SETUP, "remap setup kernel", [&] {
+        return launch_remap_setup(c->d, c->p, c->nq, P, x0, R.vel, t, R.dm[i], R.dadv[i], c->part,
+                                  c->arith, c->stream);
+    }));
     CK(launch_min_accum(c->part, nb, R.mind, reset ? 1 : 0, c->stream));
     CK(launch_mass_diag(c->d, c->p, c->nq, P, R.dm[i], c->ev64, c->arith, c->stream));
     CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx, 1,
@@ -401,7 +403,9 @@ tmop_status remap_stage(tmop_ctx *c, const double *u, int i, double *kout, const
     auto &R = c->rm;
     const ElemParams P = c->params();
     const int nb = reduce_blocks(c->Nx);
-    CK(launch_adv_apply(c->d, c->p, c->nq, P, u, R.dadv[i], c->ev64, c->arith, c->stream));
+    TRY(timed(c, TMOP_K_ADVECT, "advection kernel", [&] {
+        return launch_adv_apply(c->d, c->p, c->nq, P, u, R.dadv[i], c->ev64, c->arith, c->stream);
+    }));
     CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx, 1,
                        c->ENP, R.rhs, TMOP_FP64, nullptr, 0, c->stream));
     CK(launch_cg_init(R.rhs, R.dinv[i], c->Nx, kout, R.r, R.z, R.pv, c->part, nb, o.cg_rtol, R.cg,
@@ -411,12 +415,12 @@ tmop_status remap_stage(tmop_ctx *c, const double *u, int i, double *kout, const
     while (true) {
         const int kend = std::min(o.cg_max_it, k + chunk);
         for (int kk = k + 1; kk <= kend; ++kk) {
-            CK(launch_mass_apply(c->d, c->p, c->nq, P, R.pv, R.dm[i], c->ev64, stop, kk, c->arith,
-                                 c->stream));
-            CK(launch_assemble(c->ev64, TMOP_FP64, c->csr_ptr, c->csr_idx, nullptr, nullptr, 0, c->Nx,
-                               1, c->ENP, R.Mp, TMOP_FP64, stop, kk, c->stream));
-            CK(launch_cg_iter_scalars(R.pv, R.Mp, kout, R.r, R.z, R.dinv[i], c->Nx, c->part, nb, R.cg,
-                                      kk, o.cg_max_it, c->stream));
+            TRY(timed(c, TMOP_K_MASS, "mass kernel", [&] {
+                return launch_mass_apply(c->d, c->p, c->nq, P, R.pv, R.dm[i], c->ev64, stop, kk,
+                                         c->arith, c->stream);
+            }));
+            CK(launch_cg_iter(c->ev64, c->csr_ptr, c->csr_idx, R.pv, R.Mp, kout, R.r, R.z, R.dinv[i],
+                              c->Nx, c->part, nb, R.cg, kk, o.cg_max_it, c->stream));
         }
         CK(cudaMemcpyAsync(R.hcg, R.cg, sizeof(CgState), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));

@@ -186,6 +186,24 @@ __device__ __forceinline__ float norm(float a) { return a; }
 __device__ __forceinline__ df to_df(const dprod &a) { return fast_two_sum(a.p, a.e); }
 __device__ __forceinline__ df to_df(const df &a) { return a; }
 
+// Assembly sums.  Float element vectors are summed on the FP32 pipes in a
+// float-pair accumulator (TwoSum of the high words, low words and rounding
+// errors collected in the low word, renormalised every 8 entries): B300
+// issues FP64 adds and float-to-double conversions ~60x slower than FP32
+// ops, and the plain double sum of float entries was bound by them.  Double
+// entries are summed in double (splitting them on the integer pipe cost
+// more than it saved).
+template <class RI> struct AsmAcc { using T = double; };
+template <> struct AsmAcc<float> { using T = df; };
+__device__ __forceinline__ void asm_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void asm_zero(df &a) { a = df(0.0f, 0.0f); }
+__device__ __forceinline__ void asm_add(double &a, double v) { a += v; }
+__device__ __forceinline__ void asm_add(df &a, float v) { acc_add(a, dprod{v, 0.0f}); }
+__device__ __forceinline__ void asm_renorm(double &) {}
+__device__ __forceinline__ void asm_renorm(df &a) { a = norm(a); }
+template <class RO> __device__ __forceinline__ RO asm_out(double a) { return RO(a); }
+template <class RO> __device__ __forceinline__ RO asm_out(const df &a) { return RO(norm(a).h); }
+
 // Conversions used by the templated kernels.
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return (double)v; }

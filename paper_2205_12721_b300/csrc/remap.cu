@@ -6,7 +6,8 @@
 //                  dm = w_q det A_q and dadv_b = w_q (adj(A_q) v_q)_b, since
 //                  det A v . A^-T grad_xbar u = (adj(A) v) . grad_xbar u;
 //                  per-CTA min det A for the inversion check
-//   k_mass_apply   (M u)_e = B^T (dm * B u_e)  (B (x) B (x) B contractions)
+//   k_mass_apply   (M u)_e = B^T (dm * B u_e)  (B (x) B (x) B contractions,
+//                  compact layout of its own)
 //   k_mass_diag    sum_q dm w_i(chi_q)^2 through squared 1D tables
 //   k_adv_apply    (K u)_e = B^T (dadv . G u_e)
 // Element vectors (one component) are assembled by the transposed-map kernel.
@@ -66,24 +67,132 @@ k_remap_setup(ElemParams P, const double *__restrict__ x0, const double *__restr
     cta_energy_reduce<C>(0.0, emin, part, blockIdx.x);
 }
 
-// ev = element vectors of M u; skipped when *stop < kk (CG iterations after convergence)
+// ev = element vectors of M u; skipped when *stop < kk (CG iterations after
+// convergence).  The mass action is the inner loop of the remap CG and has
+// little arithmetic per element, so it runs with its own compact shared
+// layout (nodal values and two contraction buffers per element, no
+// Jacobian or geometry storage) for a high occupancy, values-only
+// contractions, and in 3D the q3 column kept in registers through the last
+// forward contraction, the dm scaling and the first transposed one.
+template <class C>
+struct MassLayout {
+    static constexpr int NI = C::NI, NQ = C::NQ;
+    static constexpr int SU = C::D == 3 ? NI * NI * NI : NI * NI;
+    static constexpr int S1 = C::D == 3 ? NI * NI * NQ : NI * NQ;
+    static constexpr int S2 = C::D == 3 ? NI * NQ * NQ : NQ * NQ;
+};
+
 template <class C, class R>
 __global__ void __launch_bounds__(C::NT)
 k_mass_apply(ElemParams P, const double *__restrict__ u, const double *__restrict__ dm,
              double *__restrict__ ev, const int *__restrict__ stop, int kk)
 {
     if (stop && *stop < kk) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    ElemCtx<C, R> c;
-    prologue<C, R>(P, blockIdx.x, smem, c);
-    R *f = c.sX;
-    values_at_points<C, R, double>(P, c, u, nullptr, 0, f);
-    for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
-        f[q] = prod(R(dm[c.e * C::NQD + q]), f[q]);
-    });
-    values_transpose<C, R>(c, f);
-    if (c.valid)
-        for (int i = c.t; i < C::NP; i += C::TPE) ev[c.e * C::NP + i] = to_d(c.su[i]);
+    constexpr int NI = C::NI, NQ = C::NQ;
+    using L = MassLayout<C>;
+    __shared__ R sB[NQ * NI];
+    __shared__ R su_all[C::EPB][L::SU];
+    __shared__ R s1_all[C::EPB][L::S1];
+    __shared__ R s2_all[C::EPB][L::S2];
+    const R *__restrict__ tab = table_of<R>(P);
+    for (int i = threadIdx.x; i < NQ * NI; i += C::NT) sB[i] = tab[i];
+    const int slot = threadIdx.x / C::TPE;
+    const bool act = slot < C::EPB;
+    const int sl = act ? slot : 0;
+    const int t = threadIdx.x - slot * C::TPE, tx = t % C::MX, ty = t / C::MX;
+    const int64_t e = (int64_t)blockIdx.x * C::EPB + sl;
+    const bool valid = act && e < P.E;
+    R *su = su_all[sl], *s1 = s1_all[sl], *s2 = s2_all[sl];
+    // conversions on the integer/FP32 pipes (the FP64 pipe would bound this kernel)
+    if (valid)
+        for (int i = t; i < C::NP; i += C::TPE) su[i] = from_db<R>(u[P.map[e * C::NP + i]]);
+    __syncthreads();
+    const double *__restrict__ dme = dm + e * C::NQD;
+    if (C::D == 3) {
+        if (valid && tx < NQ && ty < NI)                       // i1 -> q1
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                R a = R(0.0);
+#pragma unroll
+                for (int i1 = 0; i1 < NI; ++i1) acc_add(a, sB[tx * NI + i1] * su[(i3 * NI + ty) * NI + i1]);
+                s1[(i3 * NI + ty) * NQ + tx] = norm(a);
+            }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NQ)                       // i2 -> q2
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                R a = R(0.0);
+#pragma unroll
+                for (int i2 = 0; i2 < NI; ++i2) acc_add(a, sB[ty * NI + i2] * s1[(i3 * NI + i2) * NQ + tx]);
+                s2[(i3 * NQ + ty) * NQ + tx] = norm(a);
+            }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NQ) {                     // i3 -> q3, * dm, q3 -> i3
+            R col[NI], acc[NI];
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                col[i3] = s2[(i3 * NQ + ty) * NQ + tx];
+                acc[i3] = R(0.0);
+            }
+#pragma unroll
+            for (int q3 = 0; q3 < NQ; ++q3) {
+                R f = R(0.0);
+#pragma unroll
+                for (int i3 = 0; i3 < NI; ++i3) acc_add(f, sB[q3 * NI + i3] * col[i3]);
+                f = prod(from_db<R>(dme[(q3 * NQ + ty) * NQ + tx]), norm(f));
+#pragma unroll
+                for (int i3 = 0; i3 < NI; ++i3) acc_add(acc[i3], sB[q3 * NI + i3] * f);
+            }
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) s2[(i3 * NQ + ty) * NQ + tx] = norm(acc[i3]);
+        }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NI)                       // q2 -> i2
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                R a = R(0.0);
+#pragma unroll
+                for (int q2 = 0; q2 < NQ; ++q2) acc_add(a, sB[q2 * NI + ty] * s2[(i3 * NQ + q2) * NQ + tx]);
+                s1[(i3 * NI + ty) * NQ + tx] = norm(a);
+            }
+        __syncthreads();
+        if (valid && tx < NI && ty < NI)                       // q1 -> i1
+#pragma unroll
+            for (int i3 = 0; i3 < NI; ++i3) {
+                R a = R(0.0);
+#pragma unroll
+                for (int q1 = 0; q1 < NQ; ++q1) acc_add(a, sB[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1]);
+                ev[e * C::NP + (i3 * NI + ty) * NI + tx] = to_db(norm(a));
+            }
+    } else {
+        if (valid && tx < NQ && ty < NI) {                     // i1 -> q1
+            R a = R(0.0);
+#pragma unroll
+            for (int i1 = 0; i1 < NI; ++i1) acc_add(a, sB[tx * NI + i1] * su[ty * NI + i1]);
+            s1[ty * NQ + tx] = norm(a);
+        }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NQ) {                     // i2 -> q2, * dm
+            R a = R(0.0);
+#pragma unroll
+            for (int i2 = 0; i2 < NI; ++i2) acc_add(a, sB[ty * NI + i2] * s1[i2 * NQ + tx]);
+            s2[ty * NQ + tx] = prod(from_db<R>(dme[ty * NQ + tx]), norm(a));
+        }
+        __syncthreads();
+        if (valid && tx < NQ && ty < NI) {                     // q2 -> i2
+            R a = R(0.0);
+#pragma unroll
+            for (int q2 = 0; q2 < NQ; ++q2) acc_add(a, sB[q2 * NI + ty] * s2[q2 * NQ + tx]);
+            s1[ty * NQ + tx] = norm(a);
+        }
+        __syncthreads();
+        if (valid && tx < NI && ty < NI) {                     // q1 -> i1
+            R a = R(0.0);
+#pragma unroll
+            for (int q1 = 0; q1 < NQ; ++q1) acc_add(a, sB[q1 * NI + tx] * s1[ty * NQ + q1]);
+            ev[e * C::NP + ty * NI + tx] = to_db(norm(a));
+        }
+    }
 }
 
 template <class C, class R>
@@ -178,7 +287,17 @@ cudaError_t launch_mass_apply(int d, int p, int q, const ElemParams &P, const do
                               const double *dm, double *ev, const int *stop, int kk, int arith,
                               cudaStream_t s)
 {
-    TMOP_REMAP_LAUNCH(k_mass_apply, P, u, dm, ev, stop, kk)
+    auto run = [&](auto cfg) -> cudaError_t {
+        using C = decltype(cfg);
+        const int64_t nb = nblk<C>(P);
+        if (nb == 0) return cudaSuccess;
+        if (arith == ARITH_NATIVE)
+            k_mass_apply<C, double><<<(unsigned)nb, C::NT, 0, s>>>(P, u, dm, ev, stop, kk);
+        else
+            k_mass_apply<C, df><<<(unsigned)nb, C::NT, 0, s>>>(P, u, dm, ev, stop, kk);
+        count_launch();
+        return cudaGetLastError();
+    };
     TMOP_SWITCH(d, p, q, CASE)
 }
 

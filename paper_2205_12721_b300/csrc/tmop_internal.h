@@ -124,13 +124,14 @@ cudaError_t launch_minres_update(void *v, const void *w1, const void *w2, void *
                                  int k, cudaStream_t s);
 
 // Remap CG and RK4 vector kernels (vec_kernels.cu).  One CG iteration kk
-// (1-based) is the mass action (remap.cu) followed by launch_cg_iter_scalars.
+// (1-based) is the mass action into element vectors ev (remap.cu) followed by
+// launch_cg_iter (assembly of Mp fused with p.Mp, then the CG updates).
 cudaError_t launch_cg_init(const double *b, const double *dinv, int64_t n, double *k, double *r,
                            double *z, double *p, double *part, int nb, double rtol, CgState *st,
                            cudaStream_t s);
-cudaError_t launch_cg_iter_scalars(const double *p, const double *Mp, double *k, double *r,
-                                   double *z, const double *dinv, int64_t n, double *part, int nb,
-                                   CgState *st, int kk, int max_it, cudaStream_t s);
+cudaError_t launch_cg_iter(const double *ev, const int32_t *ptr, const int32_t *idx, double *p,
+                           double *Mp, double *k, double *r, double *z, const double *dinv, int64_t n,
+                           double *part, int nb, CgState *st, int kk, int max_it, cudaStream_t s);
 cudaError_t launch_axpy(const double *u, const double *k, double c, int64_t n, double *out,
                         cudaStream_t s);
 cudaError_t launch_rk4_combine(double *u, const double *k1, const double *k2, const double *k3,

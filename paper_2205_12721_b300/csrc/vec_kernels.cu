@@ -7,6 +7,7 @@
 #include <climits>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "minres_scalar.cuh"
 #include "tmop_internal.h"
 
@@ -43,20 +44,25 @@ __global__ void k_assemble(const RI *__restrict__ ev, const int32_t *__restrict_
     if (n >= Nx) return;
     const int b = ptr[n], e = ptr[n + 1];
     // entries in fixed order; the D component loads of an entry are independent
-    double s[3] = {0.0, 0.0, 0.0};
+    typename AsmAcc<RI>::T s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) asm_zero(s[a]);
     for (int j = b; j < e; ++j) {
         const int64_t t = __ldg(idx + j);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a < D) s[a] += (double)__ldg(ev + a * ENP + t);
+            if (a < D) asm_add(s[a], __ldg(ev + a * ENP + t));
+        if (((j - b) & 7) == 7)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= D) break;
         const int64_t dof = a * Nx + n;
-        double r = s[a];
-        if (fixed && fixed[dof]) r = (mode == 0) ? 0.0 : (mode == 1 ? (vfix ? (double)vfix[dof] : 0.0) : 1.0);
-        out[dof] = (RO)r;
+        RO r = asm_out<RO>(s[a]);
+        if (fixed && fixed[dof]) r = (mode == 0) ? RO(0) : (mode == 1 ? (vfix ? vfix[dof] : RO(0)) : RO(1));
+        out[dof] = r;
     }
 }
 
@@ -297,15 +303,23 @@ __global__ void k_cg_start(const double *__restrict__ part, int nb, double rtol,
     }
 }
 
-// partial p.Mp
-__global__ void k_cg_dot(const double *__restrict__ p, const double *__restrict__ q, int64_t n,
-                         double *__restrict__ part, const CgState *__restrict__ st, int kk)
+// Mp = assembly of the one-component element vectors ev (fixed entry order,
+// no fixed DOFs) and the partial p.Mp, in one pass
+__global__ void k_cg_assemble_dot(const double *__restrict__ ev, const int32_t *__restrict__ ptr,
+                                  const int32_t *__restrict__ idx, int64_t n,
+                                  const double *__restrict__ p, double *__restrict__ q,
+                                  double *__restrict__ part, const CgState *__restrict__ st, int kk)
 {
     if (st->stop < kk) return;
     __shared__ double sh[VT / 32];
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += p[i] * q[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = ptr[i], e = ptr[i + 1];
+        double a = 0.0;
+        for (int j = b; j < e; ++j) a += __ldg(ev + __ldg(idx + j));
+        q[i] = a;
+        s += p[i] * a;
+    }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -599,15 +613,15 @@ cudaError_t launch_cg_init(const double *b, const double *dinv, int64_t n, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_iter_scalars(const double *p, const double *Mp, double *k, double *r,
-                                   double *z, const double *dinv, int64_t n, double *part, int nb,
-                                   CgState *st, int kk, int max_it, cudaStream_t s)
+cudaError_t launch_cg_iter(const double *ev, const int32_t *ptr, const int32_t *idx, double *p,
+                           double *Mp, double *k, double *r, double *z, const double *dinv, int64_t n,
+                           double *part, int nb, CgState *st, int kk, int max_it, cudaStream_t s)
 {
-    k_cg_dot<<<nb, VT, 0, s>>>(p, Mp, n, part, st, kk);
+    k_cg_assemble_dot<<<nb, VT, 0, s>>>(ev, ptr, idx, n, p, Mp, part, st, kk);
     k_cg_alpha<<<1, VT, 0, s>>>(part, nb, st, kk);
     k_cg_update<<<nb, VT, 0, s>>>(k, r, z, p, Mp, dinv, n, part, st, kk);
     k_cg_beta<<<1, VT, 0, s>>>(part, nb, st, kk, max_it);
-    k_cg_dir<<<nb, VT, 0, s>>>(const_cast<double *>(p), z, n, st, kk);
+    k_cg_dir<<<nb, VT, 0, s>>>(p, z, n, st, kk);
     count_launch(5);
     return cudaGetLastError();
 }
