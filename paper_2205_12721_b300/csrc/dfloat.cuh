@@ -182,6 +182,20 @@ __device__ __forceinline__ df norm(const df &a) { return fast_two_sum(a.h, a.l);
 __device__ __forceinline__ double norm(double a) { return a; }
 __device__ __forceinline__ float norm(float a) { return a; }
 
+__device__ __forceinline__ df operator-(const df &a) { return df(-a.h, -a.l); }
+__device__ __forceinline__ dprod operator-(const dprod &a) { return {-a.p, -a.e}; }
+// a*b - c*d, normalised
+__device__ __forceinline__ df dw_fms(const df &a, const df &b, const df &c, const df &d)
+{
+    const dprod p = a * b, r = c * d;
+    return add_norm(p.p, -r.p, p.e - r.e);
+}
+
+// A normalised double-float value stored as the type of the stored data.
+template <class RH> __device__ __forceinline__ RH store_dw(const df &a);
+template <> __device__ __forceinline__ df store_dw<df>(const df &a) { return a; }
+template <> __device__ __forceinline__ float store_dw<float>(const df &a) { return a.h; }
+
 // Normalised value of a product.
 __device__ __forceinline__ df to_df(const dprod &a) { return fast_two_sum(a.p, a.e); }
 __device__ __forceinline__ df to_df(const df &a) { return a; }

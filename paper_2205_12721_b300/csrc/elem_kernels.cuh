@@ -14,6 +14,8 @@
 // assembled to nodes by the transposed-map kernel in vec_kernels.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "tmop_device.cuh"
 
 namespace tmop {
@@ -222,18 +224,27 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
+    const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        double T[C::DD], Cf[C::DD];
         const double ws = point_target<C>(P, c.sX, q);
         const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+        double I1, tau, I2 = 0.0;
+        if constexpr (std::is_same<RS, df>::value) {
+            if (dw) {
+                df Td[C::DD], Cd[C::DD];
+                point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+            }
+        }
+        if (!dw) {
+            double T[C::DD], Cf[C::DD];
 #pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
-        double I1, tau, I2;
-        invariants<C::D>(T, I1, tau, I2, Cf);
+            for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
+            invariants<C::D>(T, I1, tau, I2, Cf);
+        }
         const double detA = ws > 0.0 ? tau * wd : -INFINITY;   // no target: inverted
         emin = fmin(emin, detA);
         if (detA > 0.0) {
@@ -265,14 +276,40 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
+    const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
         const double ws = point_target<C>(P, c.sX, q);
         const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+        if constexpr (std::is_same<RS, df>::value) {
+            if (dw) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
+                df Td[C::DD], Cd[C::DD];
+                double I1, tau;
+                point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+                emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+                if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                    for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0f, 0.0f);
+                    return;
+                }
+                Inv v;
+                esum += cq * metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                const double sc = cq * iws;
+                const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
+#pragma unroll
+                for (int r = 0; r < C::DD; ++r) {
+                    df acc(0.0f, 0.0f);
+                    acc_add(acc, a * Td[r]);
+                    acc_add(acc, b * Cd[r]);
+                    c.sA[r * C::NQD + q] = norm(acc);
+                }
+                return;
+            }
+        }
+        double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;
@@ -321,13 +358,66 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
 
     RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
         const double ws = point_target<C>(P, c.sX, q);
         const double iws = 1.0 / ws;
         double wd = ws;
 #pragma unroll
         for (int k = 1; k < C::D; ++k) wd *= ws;
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
+        if constexpr (std::is_same<RS, df>::value && !HAS_I2 && !std::is_same<RH, double>::value) {
+            // the factored d2mu/dT2 below, on the FP32 pipes
+            df Td[C::DD], Cd[C::DD];
+            double I1, tau;
+            point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+            if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0f);
+                return;
+            }
+            Inv v;
+            metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+            const double sc = cq * iws * iws;
+            const df a1 = from_db<df>(2.0 * sc * v.f11), b1 = from_db<df>(sc * v.f1t);
+            const df a2 = from_db<df>(2.0 * sc * v.f1t), b2 = from_db<df>(sc * v.ftt);
+            const df dg = from_db<df>(2.0 * sc * v.f1), ft = from_db<df>(sc * v.ft);
+            df u[C::DD], w[C::DD];
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r) {
+                df x(0.0f, 0.0f), y(0.0f, 0.0f);
+                acc_add(x, a1 * Td[r]);
+                acc_add(x, b1 * Cd[r]);
+                acc_add(y, a2 * Td[r]);
+                acc_add(y, b2 * Cd[r]);
+                u[r] = norm(x);
+                w[r] = norm(y);
+                Td[r] = df(2.0f * Td[r].h, 2.0f * Td[r].l);    // g1 = 2T (exact)
+            }
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+                for (int s = r; s < C::DD; ++s) {
+                    const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
+                    df k(0.0f, 0.0f);
+                    acc_add(k, u[r] * Td[s]);
+                    acc_add(k, w[r] * Cd[s]);
+                    if (r == s) acc_add(k, dprod{dg.h, dg.l});
+                    if (a != cc && b != e) {
+                        if (C::D == 2) {
+                            const bool neg = (a == 0) != (b == 0);
+                            acc_add(k, neg ? dprod{-ft.h, -ft.l} : dprod{ft.h, ft.l});
+                        } else {
+                            // T = g1 / 2 at the index of the third row and column
+                            const df Tm = df(0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].h,
+                                             0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].l);
+                            const dprod pt = ft * Tm;
+                            acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
+                        }
+                    }
+                    He[pidx<C::DD>(r, s) * C::NQD + q] = store_dw<RH>(norm(k));
+                }
+            return;
+        }
+        double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
         double I1, tau, I2;

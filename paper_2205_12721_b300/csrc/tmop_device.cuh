@@ -519,6 +519,48 @@ __device__ __forceinline__ void invariants(const double *T, double &I1, double &
     }
 }
 
+// cof T in double-float (same entry order as cofactor()).
+template <int D>
+__device__ __forceinline__ void cofactor_dw(const df *T, df *Cf)
+{
+    if (D == 2) {
+        Cf[0] = T[3]; Cf[1] = -T[2]; Cf[2] = -T[1]; Cf[3] = T[0];
+    } else {
+        Cf[0] = dw_fms(T[4], T[8], T[5], T[7]);
+        Cf[1] = dw_fms(T[5], T[6], T[3], T[8]);
+        Cf[2] = dw_fms(T[3], T[7], T[4], T[6]);
+        Cf[3] = dw_fms(T[2], T[7], T[1], T[8]);
+        Cf[4] = dw_fms(T[0], T[8], T[2], T[6]);
+        Cf[5] = dw_fms(T[1], T[6], T[0], T[7]);
+        Cf[6] = dw_fms(T[1], T[5], T[2], T[4]);
+        Cf[7] = dw_fms(T[2], T[3], T[0], T[5]);
+        Cf[8] = dw_fms(T[0], T[4], T[1], T[3]);
+    }
+}
+
+// Pointwise algebra on the FP32 pipes for the metrics of (I1, tau): B300
+// issues FP64 ~60x slower than FP32, and the per-point FP64 algebra bounded
+// the energy, gradient and set-up kernels.  T = A / w from the double-float
+// Jacobian (unit: w = 1, no scaling), cof T, I1 = |T|^2 and tau = det T in
+// double-float; I1 and tau are returned in double for the metric's scalar
+// derivatives, which stay FP64.
+template <int D, int NQD>
+__device__ __forceinline__ void point_T_dw(const df *sA, int q, double iws, bool unit, df *T, df *Cf,
+                                           double &I1, double &tau)
+{
+    const df s = from_db<df>(iws);
+#pragma unroll
+    for (int r = 0; r < D * D; ++r) T[r] = unit ? sA[r * NQD + q] : to_df(sA[r * NQD + q] * s);
+    cofactor_dw<D>(T, Cf);
+    df a(0.0f, 0.0f), t(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < D * D; ++r) acc_add(a, T[r] * T[r]);
+#pragma unroll
+    for (int b = 0; b < D; ++b) acc_add(t, T[b] * Cf[b]);
+    I1 = to_db(norm(a));
+    tau = to_db(norm(t));
+}
+
 // g2 = dI2/dT = 2 (I1 T - T T^T T) (3D only).
 __device__ __forceinline__ void dI2_3(const double *T, double I1, double *g2, double *TtT,
                                       double *TTt)
