@@ -226,11 +226,14 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
     double esum = 0.0, emin = INFINITY;
     const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        const double ws = point_target<C>(P, c.sX, q);
-        const double iws = 1.0 / ws;
-        double wd = ws;
+        double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
+        if (P.target != TGT_IDENTITY) {
+            ws = point_target<C>(P, c.sX, q);
+            iws = 1.0 / ws;
+            wd = ws;
 #pragma unroll
-        for (int k = 1; k < C::D; ++k) wd *= ws;
+            for (int k = 1; k < C::D; ++k) wd *= ws;
+        }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         double I1, tau, I2 = 0.0;
         if constexpr (std::is_same<RS, df>::value) {
@@ -278,11 +281,14 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
     double esum = 0.0, emin = INFINITY;
     const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        const double ws = point_target<C>(P, c.sX, q);
-        const double iws = 1.0 / ws;
-        double wd = ws;
+        double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
+        if (P.target != TGT_IDENTITY) {
+            ws = point_target<C>(P, c.sX, q);
+            iws = 1.0 / ws;
+            wd = ws;
 #pragma unroll
-        for (int k = 1; k < C::D; ++k) wd *= ws;
+            for (int k = 1; k < C::D; ++k) wd *= ws;
+        }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         if constexpr (std::is_same<RS, df>::value) {
             if (dw) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
@@ -358,11 +364,14 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
 
     RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
-        const double ws = point_target<C>(P, c.sX, q);
-        const double iws = 1.0 / ws;
-        double wd = ws;
+        double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
+        if (P.target != TGT_IDENTITY) {
+            ws = point_target<C>(P, c.sX, q);
+            iws = 1.0 / ws;
+            wd = ws;
 #pragma unroll
-        for (int k = 1; k < C::D; ++k) wd *= ws;
+            for (int k = 1; k < C::D; ++k) wd *= ws;
+        }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         if constexpr (std::is_same<RS, df>::value && !HAS_I2 && !std::is_same<RH, double>::value) {
             // the factored d2mu/dT2 below, on the FP32 pipes

@@ -422,6 +422,19 @@ __device__ __forceinline__ void cofactor(const double *T, double *Cf)
     }
 }
 
+// tau^(-1/3) for tau > 0: a float estimate refined by two Newton steps on
+// f(y) = y^-3 - tau, y <- y (4 - tau y^3) / 3 (quadratic convergence, ~1e-7
+// -> ~1e-14 -> rounding); about 15 FP64 operations where cbrt and two
+// divisions took ~45.  Outside the float range: the library cbrt.
+__device__ __forceinline__ double rcbrt_newton(double t)
+{
+    if (!(t > 1e-30 && t < 1e30)) return 1.0 / cbrt(t);
+    double y = (double)rcbrtf((float)t);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) y = y * (4.0 - t * (y * y * y)) * (1.0 / 3.0);
+    return y;
+}
+
 // mu and the scalar derivatives for metric id at invariants (I1, tau, I2).
 // mu_7 = |T - T^-t|^2 = I1 - 2D + |T^-1|^2 (the cross term <T, T^-t> is
 // tr(T^-1 T) = D), with |T^-1|^2 = I2 / tau^2 in 3D and I1 / tau^2 in 2D;
@@ -431,6 +444,24 @@ __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, 
 {
     v.f1 = v.ft = v.f2 = v.f11 = v.f1t = v.ftt = v.f12 = v.f2t = 0.0;
     double mu = 0.0;
+    if (id == MET_303 || id == MET_303_55) {
+        const double y = rcbrt_newton(tau);           // tau^(-1/3)
+        const double c = y * y;                      // tau^(-2/3)
+        const double it = c * y;                     // 1 / tau
+        // constant factors as products (a division by a literal is a full FP64 division)
+        constexpr double k3 = 1.0 / 3.0, k9 = -2.0 / 9.0, k27 = 10.0 / 27.0;
+        mu = I1 * c * k3 - 1.0;
+        v.f1 = c * k3;
+        v.f1t = k9 * c * it;
+        v.ft = v.f1t * I1;
+        v.ftt = k27 * I1 * c * it * it;
+        if (id == MET_303_55) {
+            mu += (tau - 1.0) * (tau - 1.0);
+            v.ft += 2.0 * (tau - 1.0);
+            v.ftt += 2.0;
+        }
+        return mu;
+    }
     const double it = 1.0 / tau;
     if (id == MET_2) {
         mu = 0.5 * I1 * it - 1.0;
@@ -439,15 +470,16 @@ __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, 
         v.f1t = -0.5 * it * it;
         v.ftt = I1 * it * it * it;
     } else if (id == MET_302) {
-        const double it2 = it * it;
-        mu = I1 * I2 * it2 / 9.0 - 1.0;
-        v.f1 = I2 * it2 / 9.0;
-        v.f2 = I1 * it2 / 9.0;
-        v.ft = -2.0 * I1 * I2 * it2 * it / 9.0;
-        v.f12 = it2 / 9.0;
-        v.f1t = -2.0 * I2 * it2 * it / 9.0;
-        v.f2t = -2.0 * I1 * it2 * it / 9.0;
-        v.ftt = 2.0 * I1 * I2 * it2 * it2 / 3.0;
+        constexpr double k9 = 1.0 / 9.0;
+        const double it2 = it * it, s9 = it2 * k9;
+        mu = I1 * I2 * s9 - 1.0;
+        v.f1 = I2 * s9;
+        v.f2 = I1 * s9;
+        v.ft = -2.0 * I1 * I2 * s9 * it;
+        v.f12 = s9;
+        v.f1t = -2.0 * I2 * s9 * it;
+        v.f2t = -2.0 * I1 * s9 * it;
+        v.ftt = 6.0 * I1 * I2 * s9 * it2;
     } else if (id == MET_7 || id == MET_9) {
         const double it2 = it * it;
         const double J = (D == 3 ? I2 : I1) * it2;            // |T^-1|^2
@@ -481,21 +513,10 @@ __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, 
                 v.ftt = 2.0 * J * it;
             }
         }
-    } else {
-        if (id == MET_303 || id == MET_303_55) {
-            const double cr = cbrt(tau);
-            const double c = 1.0 / (cr * cr);        // tau^(-2/3)
-            mu += I1 * c / 3.0 - 1.0;
-            v.f1 += c / 3.0;
-            v.ft += -2.0 * I1 * c * it / 9.0;
-            v.f1t += -2.0 * c * it / 9.0;
-            v.ftt += 10.0 * I1 * c * it * it / 27.0;
-        }
-        if (id == MET_55 || id == MET_303_55) {
-            mu += (tau - 1.0) * (tau - 1.0);
-            v.ft += 2.0 * (tau - 1.0);
-            v.ftt += 2.0;
-        }
+    } else if (id == MET_55) {
+        mu = (tau - 1.0) * (tau - 1.0);
+        v.ft = 2.0 * (tau - 1.0);
+        v.ftt = 2.0;
     }
     return mu;
 }
