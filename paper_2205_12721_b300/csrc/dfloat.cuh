@@ -191,6 +191,11 @@ __device__ __forceinline__ df dw_fms(const df &a, const df &b, const df &c, cons
     return add_norm(p.p, -r.p, p.e - r.e);
 }
 
+// 2 x, exact
+__device__ __forceinline__ df twice(const df &a) { return df(2.0f * a.h, 2.0f * a.l); }
+__device__ __forceinline__ float twice(float a) { return 2.0f * a; }
+__device__ __forceinline__ double twice(double a) { return 2.0 * a; }
+
 // A normalised double-float value stored as the type of the stored data.
 template <class RH> __device__ __forceinline__ RH store_dw(const df &a);
 template <> __device__ __forceinline__ df store_dw<df>(const df &a) { return a; }

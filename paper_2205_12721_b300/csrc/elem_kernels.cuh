@@ -539,6 +539,75 @@ k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev, BatchArgs BA
     }
     __syncthreads();
     const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    if constexpr (C::D == 3) {
+        // The six (b <= e) pairs of each component a in one pass per
+        // contraction stage (3 barriers per component): the thread's q3
+        // column of each pair is read straight from the stored data and
+        // contracted in registers, then q2 and q1 through shared memory,
+        // with the pairs summed in the last stage.  Scratch: sA and sX
+        // (12 NQ^3 values >= 6 NI NQ^2 + 6 NI^2 NQ since NQ >= NI).
+        constexpr int NI = C::NI, NQ = C::NQ, GA = NI * NQ * NQ, HB = NI * NI * NQ;
+        constexpr int PB[6] = {0, 0, 0, 1, 1, 2}, PE[6] = {0, 1, 2, 1, 2, 2};
+        static_assert(6 * GA + 6 * HB <= (C::DD + C::D) * C::NQD, "diag scratch");
+        RC *g = c.sA, *h = c.sA + 6 * GA;
+        for (int a = 0; a < 3; ++a) {
+            if (c.valid && c.tx < NQ && c.ty < NQ) {          // q3 -> i3
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const RC *T3 = tbl[(PB[p] == 2) + (PE[p] == 2)];
+                    const RC *Hp = He + pidx<C::DD>(a * 3 + PB[p], a * 3 + PE[p]) * C::NQD;
+                    RC col[NQ];
+#pragma unroll
+                    for (int q3 = 0; q3 < NQ; ++q3) {
+                        const RC v = Hp[(q3 * NQ + c.ty) * NQ + c.tx];
+                        col[q3] = PB[p] == PE[p] ? v : twice(v);
+                    }
+#pragma unroll
+                    for (int i3 = 0; i3 < NI; ++i3) {
+                        RC z = RC(0.0);
+#pragma unroll
+                        for (int q3 = 0; q3 < NQ; ++q3) acc_add(z, T3[q3 * NI + i3] * col[q3]);
+                        g[p * GA + (i3 * NQ + c.ty) * NQ + c.tx] = norm(z);
+                    }
+                }
+            }
+            __syncthreads();
+            if (c.valid && c.tx < NQ && c.ty < NI) {          // q2 -> i2
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const RC *T2 = tbl[(PB[p] == 1) + (PE[p] == 1)];
+#pragma unroll
+                    for (int i3 = 0; i3 < NI; ++i3) {
+                        RC z = RC(0.0);
+#pragma unroll
+                        for (int q2 = 0; q2 < NQ; ++q2)
+                            acc_add(z, T2[q2 * NI + c.ty] * g[p * GA + (i3 * NQ + q2) * NQ + c.tx]);
+                        h[p * HB + (i3 * NI + c.ty) * NQ + c.tx] = norm(z);
+                    }
+                }
+            }
+            __syncthreads();
+            if (c.valid && c.tx < NI && c.ty < NI) {          // q1 -> i1, pairs summed
+#pragma unroll
+                for (int i3 = 0; i3 < NI; ++i3) {
+                    RC o = RC(0.0);
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) {
+                        const RC *T1 = tbl[(PB[p] == 0) + (PE[p] == 0)];
+#pragma unroll
+                        for (int q1 = 0; q1 < NQ; ++q1)
+                            acc_add(o, T1[q1 * NI + c.tx] * h[p * HB + (i3 * NI + c.ty) * NQ + q1]);
+                        o = norm(o);
+                    }
+                    RV &out = ev[(int64_t)a * P.E * C::NP + c.e * C::NP + (i3 * NI + c.ty) * NI + c.tx];
+                    if constexpr (std::is_same<RV, float>::value) out = o;
+                    else out = to_db(o);
+                }
+            }
+            __syncthreads();
+        }
+        return;
+    }
     RC *f = c.sA;
     for (int a = 0; a < C::D; ++a) {
         if (c.valid)
