@@ -113,6 +113,12 @@ cudaError_t launch_minres_scale(const void *y, const MinresState *st, int prec, 
                                 cudaStream_t s);
 cudaError_t launch_lanczos_a(void *z, const void *r1, const void *v, const MinresState *st,
                              int prec, int64_t n, int k, double *part, int nb, cudaStream_t s);
+// Assembly of the action's element vectors fused with launch_lanczos_a
+// (y = z - (beta/beta_old) r1, partial dot(v, y) over nb blocks).
+cudaError_t launch_assemble_lanczos_a(const void *ev, const int32_t *ptr, const int32_t *idx,
+                                      const uint8_t *fixed, int64_t Nx, int D, int64_t ENP, void *y,
+                                      const void *r1, const void *v, const MinresState *st, int prec,
+                                      int k, double *part, int nb, cudaStream_t s);
 cudaError_t launch_fin_alpha(const double *part, int nb, MinresState *st, int k, cudaStream_t s);
 cudaError_t launch_lanczos_b(void *y, const void *r2, const void *minv, const MinresState *st,
                              int prec, int64_t n, int k, void *ynew, double *part, int nb,

@@ -192,6 +192,49 @@ __global__ void k_lanczos_a(R *__restrict__ z, const R *__restrict__ r1, const R
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// The assembly of the action's element vectors (fixed DOFs -> 0) fused with
+// the first Lanczos update: y = z - (beta/beta_old) r1 and the partial
+// dot(v, y), one node (all components) per thread, grid-stride over nb
+// blocks.  Saves the write and re-read of z.
+template <class RI, class R>
+__global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *__restrict__ ptr,
+                                     const int32_t *__restrict__ idx, const uint8_t *__restrict__ fixed,
+                                     int64_t Nx, int D, int64_t ENP, R *__restrict__ y,
+                                     const R *__restrict__ r1, const R *__restrict__ v,
+                                     const MinresState *__restrict__ st, int k, double *__restrict__ part)
+{
+    if (st->stop_iter < k) return;
+    __shared__ double sh[VT / 32];
+    const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
+    double dsum = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < Nx; n += (int64_t)gridDim.x * blockDim.x) {
+        const int b = ptr[n], e = ptr[n + 1];
+        typename AsmAcc<RI>::T s[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) asm_zero(s[a]);
+        for (int j = b; j < e; ++j) {
+            const int64_t t = __ldg(idx + j);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (a < D) asm_add(s[a], __ldg(ev + a * ENP + t));
+            if (((j - b) & 7) == 7)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a >= D) break;
+            const int64_t dof = a * Nx + n;
+            const R z = (fixed && fixed[dof]) ? R(0) : asm_out<R>(s[a]);
+            const R yi = (R)((double)z - c * (double)r1[dof]);
+            y[dof] = yi;
+            dsum += (double)v[dof] * (double)yi;
+        }
+    }
+    dsum = block_sum(dsum, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = dsum;
+}
+
 __global__ void k_fin_alpha(const double *__restrict__ part, int nb, MinresState *st, int k)
 {
     if (st->stop_iter < k) return;
@@ -554,6 +597,23 @@ cudaError_t launch_lanczos_a(void *z, const void *r1, const void *v, const Minre
     else
         k_lanczos_a<double><<<nb, VT, 0, s>>>((double *)z, (const double *)r1, (const double *)v,
                                              st, n, k, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_lanczos_a(const void *ev, const int32_t *ptr, const int32_t *idx,
+                                      const uint8_t *fixed, int64_t Nx, int D, int64_t ENP, void *y,
+                                      const void *r1, const void *v, const MinresState *st, int prec,
+                                      int k, double *part, int nb, cudaStream_t s)
+{
+    if (prec == TMOP_FP32)
+        k_assemble_lanczos_a<float, float><<<nb, VT, 0, s>>>(
+            (const float *)ev, ptr, idx, fixed, Nx, D, ENP, (float *)y, (const float *)r1,
+            (const float *)v, st, k, part);
+    else
+        k_assemble_lanczos_a<double, double><<<nb, VT, 0, s>>>(
+            (const double *)ev, ptr, idx, fixed, Nx, D, ENP, (double *)y, (const double *)r1,
+            (const double *)v, st, k, part);
     count_launch();
     return cudaGetLastError();
 }
