@@ -1,4 +1,6 @@
 // Hessian-action kernels (the dominant kernel of the Newton step).
+#include <type_traits>
+
 #include "apply3.cuh"
 #include "elem_launch.cuh"
 
@@ -15,6 +17,16 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
         cudaError_t e = prepare(k_apply3<C, RV, RC>, L::bytes);
         if (e != cudaSuccess) return e;
         k_apply3<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k, B);
+    } else if constexpr (C::D == 3 && !(C::NI == 3 && std::is_same<RC, df>::value)) {
+        // many points per direction (9^3): the slab-column kernel.  Measured on
+        // the 24^3 Kershaw mesh, ms per action (generic -> slab): FP64 class
+        // p=1 1.90 -> 1.05, p=3 3.78 -> 2.59, p=4 4.80 -> 3.36, FP32 p=1..4
+        // 0.57/0.54/0.67/0.63 -> 0.31/0.37/0.41/0.58; FP64 class p=2 was
+        // slower (2.24 -> 2.48) and keeps the generic kernel.
+        using L = Apply3sLayout<C, RC>;
+        cudaError_t e = prepare(k_apply3s<C, RV, RC>, L::bytes);
+        if (e != cudaSuccess) return e;
+        k_apply3s<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k, B);
     } else {
         using L = Layout<C, RC>;
         cudaError_t e = prepare(k_apply<C, RV, RC>, L::bytes);
