@@ -224,7 +224,8 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
-    const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
+    const bool dw = std::is_same<RS, df>::value;
+    const bool use_i2 = metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
         if (P.target != TGT_IDENTITY) {
@@ -240,6 +241,12 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
             if (dw) {
                 df Td[C::DD], Cd[C::DD];
                 point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+                if (C::D == 3 && use_i2) {
+                    df s(0.0f, 0.0f);
+#pragma unroll
+                    for (int r = 0; r < C::DD; ++r) acc_add(s, Cd[r] * Cd[r]);
+                    I2 = to_db(norm(s));
+                }
             }
         }
         if (!dw) {
@@ -279,7 +286,8 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
-    const bool dw = std::is_same<RS, df>::value && !metric_uses_I2(P.metric, C::D);
+    const bool dw = std::is_same<RS, df>::value;
+    const bool use_i2 = metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
         if (P.target != TGT_IDENTITY) {
@@ -291,7 +299,7 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
         }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         if constexpr (std::is_same<RS, df>::value) {
-            if (dw) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
+            if (dw && !use_i2) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
                 df Td[C::DD], Cd[C::DD];
                 double I1, tau;
                 point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
@@ -313,6 +321,34 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
                     c.sA[r * C::NQD + q] = norm(acc);
                 }
                 return;
+            }
+            if constexpr (C::D == 3) {
+                if (dw && use_i2) {   // I2 metrics: + f2 dI2/dT, dI2/dT = 2 (I1 T - T T^T T)
+                    df Td[9], Cd[9], g2[9], TtT[9], TTt[9], I1w;
+                    double I1, tau;
+                    point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
+                    emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+                    if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                        for (int r = 0; r < 9; ++r) c.sA[r * C::NQD + q] = RS(0.0f, 0.0f);
+                        return;
+                    }
+                    const double I2 = i2_dw(Td, Cd, I1w, g2, TtT, TTt);
+                    Inv v;
+                    esum += cq * metric_scalars<3>(P.metric, I1, tau, I2, v);
+                    const double sc = cq * iws;
+                    const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
+                    const df c2 = from_db<df>(v.f2 * sc);
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) {
+                        df acc(0.0f, 0.0f);
+                        acc_add(acc, a * Td[r]);
+                        acc_add(acc, b * Cd[r]);
+                        acc_add(acc, c2 * g2[r]);
+                        c.sA[r * C::NQD + q] = norm(acc);
+                    }
+                    return;
+                }
             }
         }
         double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
@@ -423,6 +459,68 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                         }
                     }
                     He[pidx<C::DD>(r, s) * C::NQD + q] = store_dw<RH>(norm(k));
+                }
+            return;
+        }
+        if constexpr (std::is_same<RS, df>::value && HAS_I2 && C::D == 3 &&
+                      !std::is_same<RH, double>::value) {
+            // I2 metrics (3D): K_rs = u_r g1_s + w_r Cf_s + z_r g2_s + (2 f1 + 2 f2 I1) delta_rs
+            //   + f_tau d2tau_rs - 2 f2 (delta_ac TtT_eb + T_ae T_cb + delta_be TTt_ac),
+            // u = f11 g1 + f1t Cf + f12 g2 + 2 f2 T, w = f1t g1 + ftt Cf + f2t g2,
+            // z = f12 g1 + f2t Cf (f22 = 0), g1 = 2T: d2I2 = 4 T (x) T + 2 I1 Id - ...
+            df Td[9], Cd[9], g2w[9], TtTw[9], TTtw[9], I1w;
+            double I1, tau;
+            point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
+            if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0f);
+                return;
+            }
+            const double I2 = i2_dw(Td, Cd, I1w, g2w, TtTw, TTtw);
+            Inv v;
+            metric_scalars<3>(P.metric, I1, tau, I2, v);
+            const double sc = cq * iws * iws;
+            const df k11 = from_db<df>(2.0 * sc * v.f11), k1t = from_db<df>(sc * v.f1t);
+            const df k12 = from_db<df>(sc * v.f12), kf2 = from_db<df>(2.0 * sc * v.f2);
+            const df l1 = from_db<df>(2.0 * sc * v.f1t), ltt = from_db<df>(sc * v.ftt);
+            const df l2t = from_db<df>(sc * v.f2t), m1 = from_db<df>(2.0 * sc * v.f12);
+            const df dg = from_db<df>(2.0 * sc * (v.f1 + v.f2 * I1)), ft = from_db<df>(sc * v.ft);
+            const df m2 = from_db<df>(-2.0 * sc * v.f2);
+            df u[9], w[9], z[9];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                df x(0.0f, 0.0f), y(0.0f, 0.0f), zz(0.0f, 0.0f);
+                acc_add(x, k11 * Td[r]);          // f11 g1 (g1 = 2T)
+                acc_add(x, k1t * Cd[r]);
+                acc_add(x, k12 * g2w[r]);
+                acc_add(x, kf2 * Td[r]);          // 2 f2 T
+                acc_add(y, l1 * Td[r]);
+                acc_add(y, ltt * Cd[r]);
+                acc_add(y, l2t * g2w[r]);
+                acc_add(zz, m1 * Td[r]);
+                acc_add(zz, l2t * Cd[r]);
+                u[r] = norm(x);
+                w[r] = norm(y);
+                z[r] = norm(zz);
+            }
+#pragma unroll
+            for (int r = 0; r < 9; ++r)
+#pragma unroll
+                for (int s = r; s < 9; ++s) {
+                    const int a = r / 3, b = r % 3, cc = s / 3, e = s % 3;
+                    df k(0.0f, 0.0f);
+                    acc_add(k, u[r] * df(2.0f * Td[s].h, 2.0f * Td[s].l));
+                    acc_add(k, w[r] * Cd[s]);
+                    acc_add(k, z[r] * g2w[s]);
+                    if (r == s) acc_add(k, dprod{dg.h, dg.l});
+                    if (a != cc && b != e) {
+                        const dprod pt = ft * Td[(3 - a - cc) * 3 + (3 - b - e)];
+                        acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
+                    }
+                    if (a == cc) acc_add(k, m2 * TtTw[e * 3 + b]);
+                    acc_add(k, m2 * to_df(Td[a * 3 + e] * Td[cc * 3 + b]));
+                    if (b == e) acc_add(k, m2 * TTtw[a * 3 + cc]);
+                    He[pidx<9>(r, s) * C::NQD + q] = store_dw<RH>(norm(k));
                 }
             return;
         }

@@ -567,7 +567,7 @@ __device__ __forceinline__ void cofactor_dw(const df *T, df *Cf)
 // derivatives, which stay FP64.
 template <int D, int NQD>
 __device__ __forceinline__ void point_T_dw(const df *sA, int q, double iws, bool unit, df *T, df *Cf,
-                                           double &I1, double &tau)
+                                           double &I1, double &tau, df *I1w = nullptr)
 {
     const df s = from_db<df>(iws);
 #pragma unroll
@@ -578,8 +578,44 @@ __device__ __forceinline__ void point_T_dw(const df *sA, int q, double iws, bool
     for (int r = 0; r < D * D; ++r) acc_add(a, T[r] * T[r]);
 #pragma unroll
     for (int b = 0; b < D; ++b) acc_add(t, T[b] * Cf[b]);
-    I1 = to_db(norm(a));
+    a = norm(a);
+    if (I1w) *I1w = a;
+    I1 = to_db(a);
     tau = to_db(norm(t));
+}
+
+// 3D, double-float: I2 = |cof T|^2, T^T T, T T^T and g2 = dI2/dT = 2 (I1 T - T T^T T).
+__device__ __forceinline__ double i2_dw(const df *T, const df *Cf, const df &I1, df *g2, df *TtT,
+                                        df *TTt)
+{
+    df s(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) acc_add(s, Cf[r] * Cf[r]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            df a(0.0f, 0.0f), b(0.0f, 0.0f);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                acc_add(a, T[k * 3 + i] * T[k * 3 + j]);
+                acc_add(b, T[i * 3 + k] * T[j * 3 + k]);
+            }
+            TtT[i * 3 + j] = norm(a);
+            TTt[i * 3 + j] = norm(b);
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            df a(0.0f, 0.0f);
+            acc_add(a, I1 * T[i * 3 + j]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc_add(a, -(T[i * 3 + k] * TtT[k * 3 + j]));
+            const df n = norm(a);
+            g2[i * 3 + j] = df(2.0f * n.h, 2.0f * n.l);
+        }
+    return to_db(norm(s));
 }
 
 // g2 = dI2/dT = 2 (I1 T - T T^T T) (3D only).

@@ -175,7 +175,7 @@ def _newton_parity(m, metric, steps, target=0, h0=1.0, nq=None, max_it=200):
         ro = O.newton_step(om, xs, 1e-8, max_it)
         rg = gm.newton_step(xg, 1e-8, max_it)
         g_first = g_first or ro["grad_norm"]
-        if ro["grad_norm"] < 1e-8 * g_first:
+        if ro["grad_norm"] < 1e-8 * g_first or abs(ro["energy"]) <= 1e-12 * S:
             break        # converged: F is at rounding level, line-search tests are ties
         assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
         assert ro["minres_iters"] < max_it, "case must be well conditioned (MINRES converges)"

@@ -180,8 +180,8 @@ def test_newton_with_remap_parity(d, p, shape, metric, steps):
         ro = O.newton_step(om, xs, 1e-9, 300)
         rg = gm.newton_step(x, 1e-9, 300)
         g_first = g_first or ro["grad_norm"]
-        if ro["grad_norm"] < 1e-8 * g_first:
-            break
+        if ro["grad_norm"] < 1e-8 * g_first or abs(ro["energy"]) <= 1e-12 * O.energy(om, x_start)[3]:
+            break        # F at rounding level: the line-search tests are ties
         assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
         assert ro["minres_iters"] < 300
         assert rg["halvings"] == ro["halvings"]
