@@ -11,6 +11,8 @@
 // the unnormalised acc_add (normalised once per stored value).
 #pragma once
 
+#include <type_traits>
+
 #include "elem_kernels.cuh"
 
 namespace tmop {
@@ -24,8 +26,16 @@ struct Apply3Layout {
                                     sizeof(int) * (size_t)(C::EPB * C::NP);
 };
 
+// FP32 data with n_q <= 4: 6 CTAs per SM (80 registers, no spills; the stored
+// data loads are latency-bound and more resident warps hide them: 48^3 Q3
+// 0.428 -> 0.377 ms).  Other configurations spill at that bound.
+template <class C, class RC>
+struct Apply3MinBlocks {
+    static constexpr int value = (std::is_same<RC, float>::value && C::NQ <= 4) ? 6 : 1;
+};
+
 template <class C, class RV, class RC>
-__global__ void __launch_bounds__(C::NT)
+__global__ void __launch_bounds__(C::NT, Apply3MinBlocks<C, RC>::value)
 k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
          const int *__restrict__ stop_iter, int k, BatchArgs BA)
 {
