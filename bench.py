@@ -40,7 +40,7 @@ MINRES_ITS = 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_apply launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {"fp64": 2.780e9, "fp32": 1.393e9}
+TRAFFIC_BYTES = {"fp64": 2.780e9, "fp32": 1.394e9}
 
 
 def flops_apply_per_elem(d, ni, nq, ns):
