@@ -28,7 +28,9 @@ struct Apply3Layout {
 
 // FP32 data with n_q <= 4: 6 CTAs per SM (80 registers, no spills; the stored
 // data loads are latency-bound and more resident warps hide them: 48^3 Q3
-// 0.428 -> 0.377 ms).  Other configurations spill at that bound.
+// 0.428 -> 0.377 ms).  Other configurations spill at that bound; the
+// double-float data at 4 CTAs per SM (128 registers, small spills) measured
+// no faster (0.320 vs 0.33 of HBM).
 template <class C, class RC>
 struct Apply3MinBlocks {
     static constexpr int value = (std::is_same<RC, float>::value && C::NQ <= 4) ? 6 : 1;
