@@ -300,19 +300,31 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         if constexpr (std::is_same<RS, df>::value) {
             if (dw && !use_i2) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
-                df Td[C::DD], Cd[C::DD];
+                df Td[C::DD], Cd[C::DD], I1w, tauw;
                 double I1, tau;
-                point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+                point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau,
+                                         &I1w, &tauw);
                 emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
                 if (!(tau > 0.0) || !(ws > 0.0)) {
 #pragma unroll
                     for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0f, 0.0f);
                     return;
                 }
-                Inv v;
-                esum += cq * metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
                 const double sc = cq * iws;
-                const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
+                df a, b;
+                if (P.metric == MET_303 || P.metric == MET_303_55) {   // scalars in double-float too
+                    InvW w;
+                    const df mu = metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
+                    esum += cq * to_db(mu);
+                    const df scw = from_db<df>(sc);
+                    a = dw_mul(scw, df(2.0f * w.f1.h, 2.0f * w.f1.l));
+                    b = dw_mul(scw, w.ft);
+                } else {
+                    Inv v;
+                    esum += cq * metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                    a = from_db<df>(2.0 * v.f1 * sc);
+                    b = from_db<df>(v.ft * sc);
+                }
 #pragma unroll
                 for (int r = 0; r < C::DD; ++r) {
                     df acc(0.0f, 0.0f);
@@ -411,20 +423,38 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
         if constexpr (std::is_same<RS, df>::value && !HAS_I2 && !std::is_same<RH, double>::value) {
             // the factored d2mu/dT2 below, on the FP32 pipes
-            df Td[C::DD], Cd[C::DD];
+            df Td[C::DD], Cd[C::DD], I1w, tauw;
             double I1, tau;
-            point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau);
+            point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w,
+                                     &tauw);
             if (!(tau > 0.0) || !(ws > 0.0)) {
 #pragma unroll
                 for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0f);
                 return;
             }
-            Inv v;
-            metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
             const double sc = cq * iws * iws;
-            const df a1 = from_db<df>(2.0 * sc * v.f11), b1 = from_db<df>(sc * v.f1t);
-            const df a2 = from_db<df>(2.0 * sc * v.f1t), b2 = from_db<df>(sc * v.ftt);
-            const df dg = from_db<df>(2.0 * sc * v.f1), ft = from_db<df>(sc * v.ft);
+            df a1, b1, a2, b2, dg, ft;
+            if (P.metric == MET_303 || P.metric == MET_303_55) {     // scalars in double-float too
+                InvW w;
+                metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
+                const df scw = from_db<df>(sc);
+                a1 = df(0.0f, 0.0f);                                  // f11 = 0
+                b1 = dw_mul(scw, w.f1t);
+                a2 = df(2.0f * b1.h, 2.0f * b1.l);
+                b2 = dw_mul(scw, w.ftt);
+                const df f1s = dw_mul(scw, w.f1);
+                dg = df(2.0f * f1s.h, 2.0f * f1s.l);
+                ft = dw_mul(scw, w.ft);
+            } else {
+                Inv v;
+                metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                a1 = from_db<df>(2.0 * sc * v.f11);
+                b1 = from_db<df>(sc * v.f1t);
+                a2 = from_db<df>(2.0 * sc * v.f1t);
+                b2 = from_db<df>(sc * v.ftt);
+                dg = from_db<df>(2.0 * sc * v.f1);
+                ft = from_db<df>(sc * v.ft);
+            }
             df u[C::DD], w[C::DD];
 #pragma unroll
             for (int r = 0; r < C::DD; ++r) {

@@ -567,7 +567,8 @@ __device__ __forceinline__ void cofactor_dw(const df *T, df *Cf)
 // derivatives, which stay FP64.
 template <int D, int NQD>
 __device__ __forceinline__ void point_T_dw(const df *sA, int q, double iws, bool unit, df *T, df *Cf,
-                                           double &I1, double &tau, df *I1w = nullptr)
+                                           double &I1, double &tau, df *I1w = nullptr,
+                                           df *tauw = nullptr)
 {
     const df s = from_db<df>(iws);
 #pragma unroll
@@ -579,9 +580,48 @@ __device__ __forceinline__ void point_T_dw(const df *sA, int q, double iws, bool
 #pragma unroll
     for (int b = 0; b < D; ++b) acc_add(t, T[b] * Cf[b]);
     a = norm(a);
+    t = norm(t);
     if (I1w) *I1w = a;
+    if (tauw) *tauw = t;
     I1 = to_db(a);
-    tau = to_db(norm(t));
+    tau = to_db(t);
+}
+
+// mu_303 (+ mu_55) and its scalar derivatives in double-float, for the
+// kernels whose remaining FP64 work was these scalars: tau^(-1/3) by a float
+// estimate and two Newton steps y <- y + y (1 - tau y^3) / 3 in double-float,
+// then c = y^2 = tau^(-2/3), 1/tau = c y, mu = I1 c / 3 - 1,
+// f1 = c / 3, f1t = -2 c / (9 tau), ft = f1t I1, ftt = 10 I1 c / (27 tau^2)
+// (plus (tau - 1)^2, 2 (tau - 1), 2 for the size term).
+struct InvW {
+    df f1, ft, f1t, ftt;
+};
+__device__ __forceinline__ df dw_sub(const df &a, const df &b) { return add_norm(a.h, -b.h, a.l - b.l); }
+__device__ __forceinline__ df dw_mul(const df &a, const df &b) { return to_df(a * b); }
+__device__ __forceinline__ df metric303_dw(const df &I1, const df &tau, bool size_term, InvW &v)
+{
+    const df one(1.0f, 0.0f);
+    df y(rcbrtf(tau.h), 0.0f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const df ty3 = dw_mul(tau, dw_mul(dw_mul(y, y), y));
+        const df r = dw_sub(one, ty3);
+        y = y + dw_mul(y, dw_mul(r, from_db<df>(1.0 / 3.0)));
+    }
+    const df c = dw_mul(y, y), it = dw_mul(c, y);
+    const df k3 = from_db<df>(1.0 / 3.0), k9 = from_db<df>(-2.0 / 9.0), k27 = from_db<df>(10.0 / 27.0);
+    df mu = dw_sub(dw_mul(dw_mul(I1, c), k3), one);
+    v.f1 = dw_mul(c, k3);
+    v.f1t = dw_mul(k9, dw_mul(c, it));
+    v.ft = dw_mul(v.f1t, I1);
+    v.ftt = dw_mul(dw_mul(k27, dw_mul(I1, c)), dw_mul(it, it));
+    if (size_term) {
+        const df tm = dw_sub(tau, one);
+        mu = mu + dw_mul(tm, tm);
+        v.ft = v.ft + df(2.0f * tm.h, 2.0f * tm.l);
+        v.ftt = v.ftt + df(2.0f, 0.0f);
+    }
+    return mu;
 }
 
 // 3D, double-float: I2 = |cof T|^2, T^T T, T T^T and g2 = dI2/dT = 2 (I1 T - T T^T T).
