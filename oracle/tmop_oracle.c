@@ -11,7 +11,7 @@
  * of the benchmark load this library.  It shares no code, header or table with
  * the CUDA library and neither links nor calls it.
  *
- * Conventions (readings of the paper, listed again in the design doc):
+ * Conventions (readings of the paper where it is silent):
  *   - reference element [0,1]^d (Sec. 3.1); Gauss-Legendre quadrature;
  *     Lagrange basis on Gauss-Lobatto-Legendre nodes (node set not stated in
  *     the paper);
@@ -24,8 +24,8 @@
  * Parity pins: every function below is checked by tests/ against values the
  * paper or mathematics fixes (textbook quadrature values, complex-step
  * derivatives, zero energy of the ideal mesh, finite differences, symmetry,
- * convergence of Newton to the uniform mesh).  The one function with no
- * independent pin is marked "parity unpinned" where it is defined.
+ * convergence of Newton to the uniform mesh, exact remap of linear fields).
+ * No function is left without such a pin.
  */
 #include <math.h>
 #include <stdint.h>
