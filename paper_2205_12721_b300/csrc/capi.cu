@@ -94,6 +94,10 @@ struct tmop_ctx {
     // discrete target field and its remap (allocated on first use)
     double *eta = nullptr, *eta_t = nullptr;
     bool eta_set = false;
+    // fused energies from FP64 invariants once the Newton energy has fallen
+    // eight orders below the largest seen (a zero-energy optimum is near)
+    bool energy_fp64 = false;
+    double energy_ref = 0.0;
     double *rsrc_x0 = nullptr, *rsrc_eta0 = nullptr;
     bool remap_on = false;
     tmop_remap_opts remap_opts{4, 1e-12, 200};
@@ -128,6 +132,7 @@ struct tmop_ctx {
         P.target = desc.target;
         P.h0 = desc.target_h0;
         P.eta = eta;
+        P.energy_fp64 = energy_fp64 ? 1 : 0;
         return P;
     }
 
@@ -824,6 +829,13 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         if (st != TMOP_OK) return finish(st);
     }
     st = energy_grad_sync(c, x, c->g, &F0, &md0);
+    if (st == TMOP_OK) {
+        c->energy_ref = std::max(c->energy_ref, std::fabs(F0));
+        if (!c->energy_fp64 && std::fabs(F0) < 1e-8 * c->energy_ref) {
+            c->energy_fp64 = true;                      // from here on, and for this x too
+            st = energy_grad_sync(c, x, c->g, &F0, &md0);
+        }
+    }
     r.energy = F0;
     r.min_det = md0;
     if (st != TMOP_OK) return finish(st);

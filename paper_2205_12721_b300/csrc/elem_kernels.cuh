@@ -224,7 +224,8 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
-    const bool dw = std::is_same<RS, df>::value;
+    // the energy is formed from FP64 invariants (see metric_mu_fp64)
+    const bool dw = false;
     const bool use_i2 = metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
@@ -312,16 +313,24 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
                 }
                 const double sc = cq * iws;
                 df a, b;
+                const bool e64 = part && P.energy_fp64;
+                if (e64) {                         // energy from FP64 invariants
+                    double Tdb[C::DD];
+#pragma unroll
+                    for (int r = 0; r < C::DD; ++r) Tdb[r] = to_db(Td[r]);
+                    esum += cq * metric_mu_fp64<C::D>(P.metric, Tdb);
+                }
                 if (P.metric == MET_303 || P.metric == MET_303_55) {   // scalars in double-float too
                     InvW w;
                     const df mu = metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
-                    esum += cq * to_db(mu);
+                    if (!e64) esum += cq * to_db(mu);
                     const df scw = from_db<df>(sc);
                     a = dw_mul(scw, df(2.0f * w.f1.h, 2.0f * w.f1.l));
                     b = dw_mul(scw, w.ft);
                 } else {
                     Inv v;
-                    esum += cq * metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                    const double mu = metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                    if (!e64) esum += cq * mu;
                     a = from_db<df>(2.0 * v.f1 * sc);
                     b = from_db<df>(v.ft * sc);
                 }
@@ -347,7 +356,15 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
                     }
                     const double I2 = i2_dw(Td, Cd, I1w, g2, TtT, TTt);
                     Inv v;
-                    esum += cq * metric_scalars<3>(P.metric, I1, tau, I2, v);
+                    const double mu = metric_scalars<3>(P.metric, I1, tau, I2, v);
+                    if (part && P.energy_fp64) {   // energy from FP64 invariants
+                        double Tdb[9];
+#pragma unroll
+                        for (int r = 0; r < 9; ++r) Tdb[r] = to_db(Td[r]);
+                        esum += cq * metric_mu_fp64<3>(P.metric, Tdb);
+                    } else {
+                        esum += cq * mu;
+                    }
                     const double sc = cq * iws;
                     const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
                     const df c2 = from_db<df>(v.f2 * sc);

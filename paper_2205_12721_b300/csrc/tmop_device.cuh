@@ -62,6 +62,7 @@ struct ElemParams {
     int metric, target;
     double h0;
     const double *__restrict__ eta = nullptr;   // nodal field of the discrete target (Nx)
+    int energy_fp64 = 0;     // fused energy from FP64 invariants (near a zero-energy optimum)
 };
 
 // ---- batched launches: one grid over the element tiles of many meshes ----
@@ -519,6 +520,25 @@ __device__ __forceinline__ double metric_scalars(int id, double I1, double tau, 
         v.ftt = 2.0;
     }
     return mu;
+}
+
+template <int D>
+__device__ __forceinline__ void invariants(const double *T, double &I1, double &tau, double &I2,
+                                           double *Cf);
+
+// mu alone, in FP64 from the FP64 image of T.  The energy is the line-search
+// quantity: near a zero-energy optimum mu = O(rounding), and an error in I1
+// or tau enters mu at first order (unlike an error in T, which enters at
+// second order where dmu/dT = 0), so there I1, tau and I2 are formed in FP64
+// even when T came from double-float contractions (the double-float floor of
+// F, ~4e-15 S_F, stopped Newton short of |dF|/|dF0| = 1e-10).
+template <int D>
+__device__ __forceinline__ double metric_mu_fp64(int id, const double *T)
+{
+    double Cf[D * D], I1, tau, I2;
+    invariants<D>(T, I1, tau, I2, Cf);
+    Inv v;
+    return metric_scalars<D>(id, I1, tau, I2, v);
 }
 
 template <int D>
