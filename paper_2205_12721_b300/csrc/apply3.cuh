@@ -26,20 +26,10 @@ struct Apply3Layout {
                                     sizeof(int) * (size_t)(C::EPB * C::NP);
 };
 
-// FP32 data with n_q <= 4: 6 CTAs per SM (80 registers, no spills; the stored
-// data loads are latency-bound and more resident warps hide them: 48^3 Q3
-// 0.428 -> 0.377 ms).  Other configurations spill at that bound; the
-// double-float data at 4 CTAs per SM (128 registers, small spills) measured
-// no faster (0.320 vs 0.33 of HBM).
-template <class C, class RC>
-struct Apply3MinBlocks {
-    static constexpr int value = (std::is_same<RC, float>::value && C::NQ <= 4) ? 6 : 1;
-};
-
 template <class C, class RV, class RC>
-__global__ void __launch_bounds__(C::NT, Apply3MinBlocks<C, RC>::value)
-k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
-         const int *__restrict__ stop_iter, int k, BatchArgs BA)
+__device__ __forceinline__ void apply3_body(ElemParams P, const RV *__restrict__ v,
+                                            const RC *__restrict__ H, RV *__restrict__ ev,
+                                            const int *__restrict__ stop_iter, int k, BatchArgs BA)
 {
     static_assert(C::D == 3, "3D kernel");
     constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP, NQD = C::NQD, NS = C::NS;
@@ -228,6 +218,29 @@ k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *_
             }
         }
     }
+}
+
+// The kernels.  FP32 data with n_q <= 4 runs 6 CTAs per SM (80 registers, no
+// spills; the stored-data loads are latency-bound and more resident warps
+// hide them: 48^3 Q3 0.428 -> 0.377 ms); every other configuration keeps the
+// compiler's default register budget (an explicit minimum of one CTA per SM
+// raised several configurations to ~255 registers and slowed them).  The
+// double-float data at 4 CTAs per SM (128 registers, small spills) measured
+// no faster (0.320 vs 0.33 of HBM).
+template <class C, class RV, class RC>
+__global__ void __launch_bounds__(C::NT)
+k_apply3(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
+         const int *__restrict__ stop_iter, int k, BatchArgs BA)
+{
+    apply3_body<C, RV, RC>(P, v, H, ev, stop_iter, k, BA);
+}
+
+template <class C, class RV, class RC>
+__global__ void __launch_bounds__(C::NT, 6)
+k_apply3_occ6(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
+              const int *__restrict__ stop_iter, int k, BatchArgs BA)
+{
+    apply3_body<C, RV, RC>(P, v, H, ev, stop_iter, k, BA);
 }
 
 // ---------------------------------------------------------------------------

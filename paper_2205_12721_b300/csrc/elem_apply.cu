@@ -12,7 +12,12 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
 {
     const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
-    if constexpr (C::D == 3 && C::NQ <= 6) {
+    if constexpr (C::D == 3 && C::NQ <= 4 && std::is_same<RC, float>::value) {
+        using L = Apply3Layout<C, RC>;
+        cudaError_t e = prepare(k_apply3_occ6<C, RV, RC>, L::bytes);
+        if (e != cudaSuccess) return e;
+        k_apply3_occ6<C, RV, RC><<<(unsigned)nb, C::NT, L::bytes, s>>>(P, v, H, ev, stop, k, B);
+    } else if constexpr (C::D == 3 && C::NQ <= 6) {
         using L = Apply3Layout<C, RC>;
         cudaError_t e = prepare(k_apply3<C, RV, RC>, L::bytes);
         if (e != cudaSuccess) return e;
