@@ -75,7 +75,7 @@ def lib():
             "or_det": (I, [P, P, P, I64, P]),
             "or_gradient": (I, [P, P, P, P, I64, P, P]),
             "or_hessian_apply": (I, [P, P, P, P, I64, P, P]),
-            "or_hessian_diag": (I, [P, P, P, I64, P]),
+            "or_hessian_diag": (I, [P, P, P, I64, P, P]),
             "or_hess_cache_build": (P, [P, P, P]),
             "or_hess_cache_free": (None, [P]),
             "or_hessian_apply_cached": (I, [P, P, P, P, P]),
@@ -230,14 +230,14 @@ def hessian_apply(m: Mesh, x, v, elems=None, with_abs=False):
     return (y, a) if with_abs else y
 
 
-def hessian_diag(m: Mesh, x, elems=None):
+def hessian_diag(m: Mesh, x, elems=None, with_abs=False):
     x = _f64(x)
     e, ne = _elems(elems)
-    dg = np.zeros(m.ndof)
-    st = lib().or_hessian_diag(m.ref(), _p(x), _p(e), ne, _p(dg))
+    dg = np.zeros(m.ndof); a = np.zeros(m.ndof) if with_abs else None
+    st = lib().or_hessian_diag(m.ref(), _p(x), _p(e), ne, _p(dg), _p(a))
     if st:
         raise RuntimeError(f"oracle hessian_diag status {st}")
-    return dg
+    return (dg, a) if with_abs else dg
 
 
 def dense_hessian(m: Mesh, x):

@@ -572,7 +572,10 @@ int or_energy(const or_mesh *M, const double *x, const double *xw, const int64_t
     return OR_OK;
 }
 
-/* Per-point det A over the listed elements, out[k*Nqd + q]. */
+/* det A at every quadrature point of the listed elements, out[k*Nqd + q]
+ * (Sec. 2.2, eq. A: A = sum_i x_{E,i} grad w_i^T, the Jacobian of the map from
+ * the reference element; det A > 0 is the validity condition the line search
+ * of Sec. 2.3 enforces). */
 int or_det(const or_mesh *M, const double *x, const int64_t *elems, int64_t n_elems, double *out)
 {
     or_tables t;
@@ -811,10 +814,12 @@ int or_hessian_apply_cached(const or_mesh *M, const double *x, const double *HA,
 /* ------------------------------------------------------------------------
  * Hessian diagonal (Sec. 3.4, Jacobi preconditioning):
  *   diag_{a,i} = sum_q sum_{b,e} H^A_{ab,ae} d_b w_i d_e w_i, assembled;
+ * absd (optional) receives the same sum of the absolute values of every
+ * term, the scale of the condition-aware tolerance;
  * 1 on fixed DOFs.
  * --------------------------------------------------------------------- */
 int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int64_t n_elems,
-                    double *diag)
+                    double *diag, double *absd)
 {
     or_tables t;
     int st = tables_build(M, &t);
@@ -823,6 +828,7 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
     int d = t.d, dd = d * d;
     int64_t ndof = (int64_t)d * M->num_nodes;
     memset(diag, 0, sizeof(double) * ndof);
+    if (absd) memset(absd, 0, sizeof(double) * ndof);
     double *xe = malloc(sizeof(double) * d * t.np);
     int rc = OR_OK;
     for (int64_t k = 0; k < n_elems; ++k) {
@@ -838,7 +844,10 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
                 for (int i = 0; i < t.np; ++i) {
                     int64_t node = M->map[e * t.np + i];
                     double ph = t.phi[q * t.np + i];
-                    for (int a = 0; a < d; ++a) diag[a * M->num_nodes + node] += c2 * ph * ph;
+                    for (int a = 0; a < d; ++a) {
+                        diag[a * M->num_nodes + node] += c2 * ph * ph;
+                        if (absd) absd[a * M->num_nodes + node] += fabs(c2 * ph * ph);
+                    }
                 }
             }
             double HA[81];
@@ -847,17 +856,25 @@ int or_hessian_diag(const or_mesh *M, const double *x, const int64_t *elems, int
                 int64_t node = M->map[e * t.np + i];
                 const double *gi = t.dphi + (q * t.np + i) * d;
                 for (int a = 0; a < d; ++a) {
-                    double s = 0;
+                    double s = 0, sa = 0;
                     for (int b = 0; b < d; ++b)
-                        for (int e2 = 0; e2 < d; ++e2) s += HA[(a * d + b) * dd + a * d + e2] * gi[b] * gi[e2];
+                        for (int e2 = 0; e2 < d; ++e2) {
+                            const double term = HA[(a * d + b) * dd + a * d + e2] * gi[b] * gi[e2];
+                            s += term;
+                            sa += fabs(term);
+                        }
                     diag[a * M->num_nodes + node] += s;
+                    if (absd) absd[a * M->num_nodes + node] += sa;
                 }
             }
         }
     }
     if (M->fixed)
         for (int64_t j = 0; j < ndof; ++j)
-            if (M->fixed[j]) diag[j] = 1.0;
+            if (M->fixed[j]) {
+                diag[j] = 1.0;
+                if (absd) absd[j] = 1.0;
+            }
     free(xe); tables_free(&t);
     return rc;
 }
@@ -1176,7 +1193,7 @@ int or_newton_step(const or_mesh *M, double *x, double minres_rtol, int minres_m
         return OR_OK;
     }
     double *HA = or_hess_cache_build(M, x, &st);
-    or_hessian_diag(M, x, NULL, 0, diag);
+    or_hessian_diag(M, x, NULL, 0, diag, NULL);
     int its = 0;
     double res = 0;
     int mst = or_minres(M, x, HA, diag, g, minres_rtol, minres_max_it, minres_fixed_its, dx, &its, &res);

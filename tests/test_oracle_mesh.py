@@ -263,3 +263,36 @@ def test_inverted_mesh_reports_status(oracle_mod):
     x2 = x.copy()
     r = oracle_mod.newton_step(M, x2)
     assert r["status"] == oracle_mod.ERR_INVERTED and np.array_equal(x, x2)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_det_affine_and_bilinear(oracle_mod, d):
+    """det A at the points (Sec. 2.2, eq. A), pinned by closed forms.
+    Affine element x = B xi + c: det A = det B at every point.  Map
+    x_1 = xi_1 (1 + alpha xi_2), other coordinates unchanged (degree 1 in each
+    reference variable, so Q_p reproduces it exactly): det A = 1 + alpha xi_2
+    at the point, with xi_2 the Gauss point of the second direction, which
+    fixes the point order q = q1 + nq q2 (+ nq^2 q3) and catches a transposed
+    Jacobian (that would give 1 + alpha xi_1)."""
+    rng = np.random.default_rng(11)
+    for order in (1, 2, 3):
+        m = mg.structured(d, order, 1)
+        nq = order + 1
+        B = np.eye(d) + 0.3 * rng.standard_normal((d, d))
+        if np.linalg.det(B) < 0:
+            B[:, 0] *= -1
+        x = mg.rigid_map(m, B, 1.0, shift=rng.standard_normal(d))
+        M = _om(oracle_mod, m, 2 if d == 2 else 303, nq, fixed=False)
+        det = oracle_mod.det(M, x)
+        assert det.shape == (1, nq ** d)
+        np.testing.assert_allclose(det, np.linalg.det(B), rtol=1e-13)
+        alpha = 0.4
+        xr = m.x.reshape(d, -1).copy()            # the unit element: x = xi
+        xb = xr.copy()
+        xb[0] = xr[0] * (1.0 + alpha * xr[1])
+        det = oracle_mod.det(M, xb.reshape(-1))[0]
+        g, _ = oracle_mod.gauss_legendre(nq)
+        q = np.arange(nq ** d)
+        xi2 = g[(q // nq) % nq]
+        np.testing.assert_allclose(det, 1.0 + alpha * xi2, rtol=1e-13)
+        assert not np.allclose(det, 1.0 + alpha * g[q % nq])
