@@ -194,6 +194,20 @@ tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag);
 tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *opts,
                              tmop_step_report *rep);
 
+/* det(A) at every quadrature point of the mesh x (Sec. 2.2, eq. A:
+ * A = sum_i x_{E,i} grad(w_i)^T, the Jacobian of the reference-to-physical
+ * map; det A > 0 everywhere is the validity condition that the line search of
+ * Sec. 2.3 enforces).  A diagnostic export of the quantity whose minimum
+ * tmop_energy returns.
+ *   x    device FP64, dim * num_nodes.
+ *   det  device FP64, num_elems * nq1d^dim, caller-owned:
+ *        det[e * nq1d^dim + q] with q = q1 + nq1d q2 (+ nq1d^2 q3), the
+ *        lexicographic point index.  Computed as det(T) det(W) from the FP64
+ *        invariants of T = A W^-1 (W = I for the identity target).
+ * Asynchronous.  Errors: TMOP_ERR_ARG (NULL pointer, discrete target without
+ * a field). */
+tmop_status tmop_det(tmop_ctx *ctx, const double *x, double *det);
+
 /* Energy and min det(A) without allocating anything (the paper has no
  * counterpart: this exists for callers of this library that cannot call
  * cudaMalloc, e.g. code running inside an application whose memory pool has

@@ -31,7 +31,7 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
            "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
            "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference",
-           "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap")
+           "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det")
 
 
 class TmopError(RuntimeError):
@@ -112,6 +112,7 @@ def lib():
             "tmop_setup": (I, [ctypes.POINTER(Desc), P, P, P, ctypes.POINTER(P)]),
             "tmop_energy": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "tmop_gradient": (I, [P, P, P]),
+            "tmop_det": (I, [P, P, P]),
             "tmop_hessian_setup": (I, [P, P]),
             "tmop_hessian_apply": (I, [P, P, P]),
             "tmop_hessian_diag": (I, [P, P]),
@@ -192,6 +193,11 @@ def tmop_energy(ctx: int, x, check: bool = True):
     if check and st not in (OK, ERR_INVERTED):
         _check(st, "tmop_energy")
     return st, F.value, md.value
+
+
+def tmop_det(ctx: int, x, det):
+    """det(A) at every quadrature point into det (device FP64, E * nq1d^dim)."""
+    _check(lib().tmop_det(ctx, _ptr(x), _ptr(det)), "tmop_det")
 
 
 def tmop_gradient(ctx: int, x, g):

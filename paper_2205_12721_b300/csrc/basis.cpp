@@ -102,4 +102,33 @@ void host_basis_tables(int ni, int nq, double *B, double *G, double *w1d)
     }
 }
 
+// Collocated derivative on the Gauss points: D_qk = m_k'(chi_q) for the
+// Lagrange polynomials m_k through the nq Gauss-Legendre points (barycentric
+// form).  A polynomial of degree < nq is reproduced exactly by its values at
+// the points, so G = D B for the GLL basis of any order p <= nq - 1 (the
+// reference gradient of a nodal field is D applied to its values at the
+// points).  Long double, stored FP64.
+void host_colloc_deriv(int nq, double *D)
+{
+    double pts[16], w[16];
+    host_gauss_legendre(nq, pts, w);
+    long double lam[16];
+    for (int k = 0; k < nq; ++k) {
+        long double p = 1.0L;
+        for (int m = 0; m < nq; ++m)
+            if (m != k) p *= (long double)pts[k] - pts[m];
+        lam[k] = 1.0L / p;
+    }
+    for (int q = 0; q < nq; ++q) {
+        long double diag = 0.0L;
+        for (int k = 0; k < nq; ++k) {
+            if (k == q) continue;
+            const long double dqk = (long double)pts[q] - pts[k];
+            D[q * nq + k] = (double)(lam[k] / (lam[q] * dqk));
+            diag += 1.0L / dqk;
+        }
+        D[q * nq + q] = (double)diag;
+    }
+}
+
 }  // namespace tmop

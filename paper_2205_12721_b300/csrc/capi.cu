@@ -768,6 +768,18 @@ tmop_status tmop_energy(tmop_ctx *ctx, const double *x, double *F, double *min_d
     return st;
 }
 
+tmop_status tmop_det(tmop_ctx *ctx, const double *x, double *det)
+{
+    if (!ctx || !x || !det) return fail(TMOP_ERR_ARG, "NULL argument");
+    TRY(target_ready(ctx));
+    ElemParams P = ctx->params();
+    P.detq = det;
+    TRY(timed(ctx, TMOP_K_ENERGY, "det kernel", [&] {
+        return launch_energy(ctx->d, ctx->p, ctx->nq, P, x, ctx->part, ctx->arith, ctx->stream);
+    }));
+    return TMOP_OK;
+}
+
 tmop_status tmop_gradient(tmop_ctx *ctx, const double *x, double *g)
 {
     if (!ctx || !x || !g) return fail(TMOP_ERR_ARG, "NULL argument");

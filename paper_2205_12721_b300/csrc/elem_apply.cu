@@ -1,10 +1,41 @@
 // Hessian-action kernels (the dominant kernel of the Newton step).
 #include <type_traits>
 
+#include <cstdlib>
+
 #include "apply3.cuh"
+#include "apply3c.cuh"
 #include "elem_launch.cuh"
 
 namespace tmop {
+
+// Tables of the collocated action for one (RC, NI, NQ), built once per process.
+template <class RC, int NI, int NQ>
+static const ColTab<RC, NI, NQ> &coltab()
+{
+    static const ColTab<RC, NI, NQ> T = [] {
+        ColTab<RC, NI, NQ> t;
+        double B[NQ * NI], G[NQ * NI], w[NQ], D[NQ * NQ];
+        host_basis_tables(NI, NQ, B, G, w);
+        host_colloc_deriv(NQ, D);
+        for (int i = 0; i < NQ * NI; ++i) t.B[i] = RC(B[i]);
+        for (int i = 0; i < NQ * NQ; ++i) t.D[i] = RC(D[i]);
+        return t;
+    }();
+    return T;
+}
+
+// Action kernel variant: 0 = register-column / slab kernels, 1 = collocated
+// warp-synchronous kernel, 2 = the same with bit-level double <-> pair
+// conversions.  TMOP_APPLY_VARIANT overrides the default for measurements.
+static int apply_variant_default()
+{
+    static const int v = [] {
+        const char *s = std::getenv("TMOP_APPLY_VARIANT");
+        return s ? std::atoi(s) : -1;
+    }();
+    return v;
+}
 
 template <class C, class RV, class RC>
 static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
@@ -12,6 +43,39 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
 {
     const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;
+    if constexpr (C::D == 3 && C::NQ * C::NQ <= 32) {
+        int var = apply_variant_default();
+        if (var < 0) var = 1;
+        if (var >= 1) {
+            using S = Apply3cShape<C>;
+            const auto &T = coltab<RC, C::NI, C::NQ>();
+            auto go = [&](auto kern, bool ga, bool sc = false, bool cp = false) {
+                const size_t bytes = S::template bytes<RC>(ga, sc, cp);
+                cudaError_t e = prepare(kern, bytes);
+                if (e != cudaSuccess) return e;
+                kern<<<(unsigned)nb, S::NT, bytes, s>>>(P, v, H, ev, stop, k, B, T);
+                count_launch();
+                return cudaGetLastError();
+            };
+            constexpr bool F32 = std::is_same<RC, float>::value;
+            switch (var) {
+                case 3: return go(k_apply3c<C, RV, RC, false, F32 ? 6 : 4>, false);
+                case 5: return go(k_apply3c<C, RV, RC, false, 0, 1, false>, false);
+                case 6: return go(k_apply3c<C, RV, RC, false, 0, 0, true>, true);
+                case 7: return go(k_apply3c<C, RV, RC, false, 0, 1, true>, true);
+                case 8: return go(k_apply3c<C, RV, RC, false, 0, 2, true>, true);
+                case 9: return go(k_apply3c<C, RV, RC, false, 0, 0, false, true>, false, true);
+                case 10: return go(k_apply3c<C, RV, RC, false, F32 ? 6 : 4, 0, false, true>, false, true);
+                case 11: return go(k_apply3c<C, RV, RC, false, F32 ? 8 : 5, 0, false, true>, false, true);
+                case 12: return go(k_apply3c<C, RV, RC, false, 0, 0, false, false, 1>, false, false, true);
+                case 13: return go(k_apply3c<C, RV, RC, false, 0, 0, false, false, 2>, false, false, true);
+                case 14: return go(k_apply3c<C, RV, RC, false, 0, 0, false, true, 1>, false, true, true);
+                case 15: return go(k_apply3c<C, RV, RC, false, 0, 0, false, true, 0, true>, false, true);
+                case 16: return go(k_apply3c<C, RV, RC, false, F32 ? 6 : 4, 0, false, true, 0, true>, false, true);
+                default: return go(k_apply3c<C, RV, RC, false, 0>, false);
+            }
+        }
+    }
     if constexpr (C::D == 3 && C::NQ <= 4 && std::is_same<RC, float>::value) {
         using L = Apply3Layout<C, RC>;
         cudaError_t e = prepare(k_apply3_occ6<C, RV, RC>, L::bytes);

@@ -64,13 +64,21 @@ __device__ __forceinline__ void prologue(const ElemParams &P, int64_t tile, unsi
 
 // Gather one component of an L-vector into the slot and run the forward
 // contractions: sA[(a*D + b)*NQD + q] = d u_a / d xbar_b at q; sX holds the
-// interpolated values when xv is requested.
-template <class C, class R, class RIN>
+// interpolated values when xv is requested.  LOCAL (positions): the element's
+// first node is subtracted in FP64 before the contractions, so that the
+// Jacobian is formed from differences of size h rather than from absolute
+// coordinates (sum_i grad w_i = 0 makes it the same A; the interpolated
+// values get the offset back).  This removes the cancellation that would
+// otherwise scale the rounding of the double-float contractions by |x|/h.
+template <class C, class R, class RIN, bool LOCAL = false>
 __device__ __forceinline__ void forward_component(const ElemParams &P, ElemCtx<C, R> &c,
                                                   const RIN *__restrict__ u, int a, bool want_x)
 {
+    double off = 0.0;
+    if (LOCAL && c.valid) off = (double)u[a * P.Nx + c.smap[0]];
     if (c.valid)
-        for (int i = c.t; i < C::NP; i += C::TPE) c.su[i] = R(u[a * P.Nx + c.smap[i]]);
+        for (int i = c.t; i < C::NP; i += C::TPE)
+            c.su[i] = LOCAL ? R((double)u[a * P.Nx + c.smap[i]] - off) : R(u[a * P.Nx + c.smap[i]]);
     __syncthreads();
     R *A0 = c.sA + (a * C::D) * C::NQD;
     R *xv = want_x ? c.sX + a * C::NQD : nullptr;
@@ -79,6 +87,18 @@ __device__ __forceinline__ void forward_component(const ElemParams &P, ElemCtx<C
                    c.valid);
     else
         fwd2<C, R>(c.B, c.G, c.su, c.s1, A0, A0 + C::NQD, xv, c.tx, c.ty, c.valid);
+    if (LOCAL && want_x && c.valid && c.tx < C::NQ && c.ty < C::NQ) {
+        // each thread restores the points it wrote (its own (q1, q2) column)
+        if (C::D == 3) {
+            for (int q3 = 0; q3 < C::NQ; ++q3) {
+                const int q = (q3 * C::NQ + c.ty) * C::NQ + c.tx;
+                xv[q] = R(to_d(xv[q]) + off);
+            }
+        } else {
+            const int q = c.ty * C::NQ + c.tx;
+            xv[q] = R(to_d(xv[q]) + off);
+        }
+    }
 }
 
 // Forward pass of the element geometry: the Jacobian rows of x into sA;
@@ -100,7 +120,7 @@ __device__ __forceinline__ void forward_geometry(const ElemParams &P, ElemCtx<C,
             fwd2<C, R>(c.B, c.G, c.su, c.s1, c.sA, c.sA + C::NQD, c.sX, c.tx, c.ty, c.valid);
     }
     const bool want_x = P.target == TGT_SIZE;
-    for (int a = 0; a < C::D; ++a) forward_component<C, R, double>(P, c, x, a, want_x);
+    for (int a = 0; a < C::D; ++a) forward_component<C, R, double, true>(P, c, x, a, want_x);
 }
 
 // Values at the points of component a of an L-vector u (minus u0 when given):
@@ -257,6 +277,7 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
             invariants<C::D>(T, I1, tau, I2, Cf);
         }
         const double detA = ws > 0.0 ? tau * wd : -INFINITY;   // no target: inverted
+        if (P.detq) P.detq[c.e * C::NQD + q] = tau * wd;         // det A = det T det W
         emin = fmin(emin, detA);
         if (detA > 0.0) {
             Inv v;

@@ -42,8 +42,11 @@ struct Cfg {
     static constexpr int DD = D * D;
     static constexpr int NS = DD * (DD + 1) / 2;            // packed symmetric H
     static constexpr int TPE = MX * MX;                      // threads per element
-    // elements per CTA: ~128 threads in 3D, ~256 in 2D
-    static constexpr int EPB_ = (D == 3 ? 128 : 256) / TPE;
+    // elements per CTA: ~128 threads in 3D, ~256 in 2D.  In 3D, when an
+    // element fits in a warp, whole elements per warp (4 warps per CTA), so
+    // that the warp-synchronous action kernel can use the same tiles.
+    static constexpr int EPW = TPE <= 32 ? 32 / TPE : 0;
+    static constexpr int EPB_ = (D == 3 && EPW > 0) ? 4 * EPW : (D == 3 ? 128 : 256) / TPE;
     static constexpr int EPB = EPB_ < 1 ? 1 : EPB_;
     static constexpr int NT = ((EPB * TPE + 31) / 32) * 32;  // CTA size, whole warps
     // per-element shared scratch (in elements of the compute type)
@@ -63,6 +66,7 @@ struct ElemParams {
     double h0;
     const double *__restrict__ eta = nullptr;   // nodal field of the discrete target (Nx)
     int energy_fp64 = 0;     // fused energy from FP64 invariants (near a zero-energy optimum)
+    double *__restrict__ detq = nullptr;        // k_energy: det A at every point (E x NQD) when set
 };
 
 // ---- batched launches: one grid over the element tiles of many meshes ----

@@ -73,6 +73,7 @@ cudaError_t launch_adv_apply(int d, int p, int q, const ElemParams &P, const dou
 void host_gauss_legendre(int n, double *x, double *w);
 void host_gll_nodes(int n, double *x);
 void host_basis_tables(int ni, int nq, double *B, double *G, double *w1d);
+void host_colloc_deriv(int nq, double *D);
 
 // MINRES scalar state kept on the device.
 struct MinresState {

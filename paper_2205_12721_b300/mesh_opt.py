@@ -87,6 +87,14 @@ class TmopMesh:
         """(status, F, min det A)."""
         return capi.tmop_energy(self.ctx, x)
 
+    def det(self, x, out=None):
+        """det(A) at every quadrature point, shape (num_elems, nq1d**dim)."""
+        nqd = self.nq1d ** self.dim
+        d = out if out is not None else torch.empty(self.num_elems * nqd, dtype=torch.float64,
+                                                    device=self.device)
+        capi.tmop_det(self.ctx, x, d)
+        return d.view(self.num_elems, nqd)
+
     def gradient(self, x, out=None):
         g = out if out is not None else torch.empty(self.ndof, dtype=torch.float64, device=self.device)
         capi.tmop_gradient(self.ctx, x, g)

@@ -36,7 +36,18 @@ def host(t):
 
 
 def assert_vec_close(gpu, ref, scale, tol=TOL, what=""):
-    """||gpu - ref||_2 <= tol * max(||ref||_2, ||scale||_2)."""
+    """Entry by entry, |gpu_i - ref_i| <= tol * max(|ref_i|, |scale_i|) + floor
+    (scale_i: the same sum evaluated with absolute values, so an entry formed by
+    cancellation is judged against the size of its terms; floor = tol * 1e-3 *
+    max|scale|, below the rounding of any entry of that size); and the l2 form
+    ||gpu - ref||_2 <= tol * max(||ref||_2, ||scale||_2)."""
+    gpu, ref, scale = (np.asarray(a, dtype=np.float64) for a in (gpu, ref, scale))
     err = np.linalg.norm(gpu - ref)
     bound = tol * max(np.linalg.norm(ref), np.linalg.norm(scale), 1e-300)
     assert err <= bound, f"{what}: |diff| = {err:.3e} > {bound:.3e} (|ref| = {np.linalg.norm(ref):.3e})"
+    floor = tol * 1e-3 * max(float(np.abs(scale).max(initial=0.0)), 1e-300)
+    ent = np.abs(gpu - ref)
+    lim = tol * np.maximum(np.abs(ref), np.abs(scale)) + floor
+    bad = np.flatnonzero(ent > lim)
+    assert bad.size == 0, (f"{what}: {bad.size} entries off, worst i={bad[np.argmax(ent[bad] / lim[bad])]}"
+                           f" diff {ent[bad].max():.3e}, limit there {lim[bad][np.argmax(ent[bad])]:.3e}")

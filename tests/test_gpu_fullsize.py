@@ -38,6 +38,9 @@ def test_fullsize_sampled_parity(cfg):
     assert abs(F - F_o) <= TOL * max(F_o, S)
     assert abs(md - md_o) <= TOL * md_o
     elems, dofs = _sample(m, 60, cfg)
+    det = host(gm.det(x))[elems]
+    det_o = O.det(om, m.x, elems=elems)
+    assert np.all(np.abs(det - det_o) <= TOL * np.abs(det_o)), "det A (sampled elements)"
     g_o, ga = O.gradient(om, m.x, elems=elems, with_abs=True)
     g = host(gm.gradient(x))
     assert_vec_close(g[dofs], g_o[dofs], ga[dofs], what="gradient (sampled)")
@@ -47,8 +50,8 @@ def test_fullsize_sampled_parity(cfg):
     y_o, ya = O.hessian_apply(om, m.x, v, elems=elems, with_abs=True)
     assert_vec_close(y[dofs], y_o[dofs], ya[dofs], what="apply (sampled)")
     dg = host(gm.hessian_diag())
-    dg_o = O.hessian_diag(om, m.x, elems=elems)
-    assert_vec_close(dg[dofs], dg_o[dofs], np.abs(dg_o[dofs]), what="diag (sampled)")
+    dg_o, dga = O.hessian_diag(om, m.x, elems=elems, with_abs=True)
+    assert_vec_close(dg[dofs], dg_o[dofs], dga[dofs], what="diag (sampled)")
     gm.close()
     if cfg == 3:
         g32 = gpu_mesh(m, metric, precision="fp32")

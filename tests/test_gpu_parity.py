@@ -60,6 +60,12 @@ def test_fp64_parity(case, precision):
         assert st == capi.OK
         assert abs(F - F_o) <= TOL * max(abs(F_o), S), (F, F_o, S)
         assert abs(md - md_o) <= TOL * abs(md_o)
+        # det A at every quadrature point (relative, per point)
+        det_o = O.det(om, m.x)
+        det = host(gm.det(x))
+        assert det.shape == det_o.shape
+        assert np.all(np.abs(det - det_o) <= TOL * np.abs(det_o)), np.abs(det / det_o - 1).max()
+        assert det.min() == md
         # gradient
         g_o, ga = O.gradient(om, m.x, with_abs=True)
         g = host(gm.gradient(x))
@@ -73,9 +79,9 @@ def test_fp64_parity(case, precision):
         assert_vec_close(y, y_o, ya, what="hessian_apply")
         assert np.array_equal(y[m.fixed != 0], v[m.fixed != 0])
         # diagonal
-        dg_o = O.hessian_diag(om, m.x)
+        dg_o, dga = O.hessian_diag(om, m.x, with_abs=True)
         dg = host(gm.hessian_diag())
-        assert_vec_close(dg, dg_o, np.abs(dg_o), what="diag")
+        assert_vec_close(dg, dg_o, dga, what="diag")
         gm.close()
 
 
@@ -98,8 +104,8 @@ def test_fp32_hessian_data(case):
     y = host(gm.hessian_apply(dev(v, torch.float32)))
     assert_vec_close(y, y_o, ya, tol=2e-6, what="fp32 apply")
     dg = host(gm.hessian_diag())
-    dg_o = O.hessian_diag(om, m.x)
-    assert_vec_close(dg, dg_o, np.abs(dg_o), tol=2e-6, what="fp32 diag")
+    dg_o, dga = O.hessian_diag(om, m.x, with_abs=True)
+    assert_vec_close(dg, dg_o, dga, tol=2e-6, what="fp32 diag")
     # energy and gradient stay FP64 in the mixed mode
     st_o, F_o, _, S = O.energy(om, m.x)
     st, F, _ = gm.energy(x)
@@ -241,6 +247,40 @@ def test_cfg1_solve_reaches_uniform_mesh():
     gm.close()
 
 
+def test_cfg1_newton_steps_fixed_minres():
+    """Per-step iterates on the 2D 8x8 Q2 configuration itself (+-0.15h, mu_2,
+    10 Newton steps).  Each step starts both sides from the same x (the
+    oracle's) and runs exactly 10 MINRES iterations (paper Sec. 2.3 with a
+    fixed inner iteration count), where the Krylov iterate is not yet
+    sensitive to rounding; the accepted x+ must agree to 1e-10 h, and the step
+    reports (energy, |dF|, halvings) must agree.  |dF| is compared at 1e-12 of
+    max(|dF|, ||abs-sum scale||) plus 1e-13 |dF(x0)|: near the optimum
+    dmu/dT -> 0 by cancellation of terms of size |T|/tau that do not shrink,
+    so its rounding stays at the level of the first gradient."""
+    from paper_2205_12721_b300 import meshgen as mg
+    m = mg.config_mesh(1)
+    om = oracle_mesh(m, 2)
+    gm = gpu_mesh(m, 2)
+    xo = m.x.copy()
+    g_first = None
+    for k in range(10):
+        S = O.energy(om, xo)[3]
+        ga = O.gradient(om, xo, with_abs=True)[1]       # abs-sum scale of dF
+        xg = dev(xo)
+        ro = O.newton_step(om, xo, 0.0, 10, True)
+        rg = gm.newton_step(xg, 0.0, 10, True)
+        assert ro["status"] == 0 and rg["status"] == 0, (k, ro, rg)
+        assert ro["minres_iters"] == rg["minres_iters"] == 10
+        assert rg["halvings"] == ro["halvings"], (k, ro, rg)
+        assert abs(rg["energy"] - ro["energy"]) <= TOL * max(ro["energy"], S)
+        g_first = g_first or ro["grad_norm"]
+        assert abs(rg["grad_norm"] - ro["grad_norm"]) <= (TOL * max(ro["grad_norm"], np.linalg.norm(ga))
+                                                          + 1e-13 * g_first), k
+        err = np.abs(host(xg) - xo).max()
+        assert err <= 1e-10 * m.h, (k, err)
+    gm.close()
+
+
 @pytest.mark.parametrize("p,nq,prec", [(1, 9, "fp64"), (2, 9, "fp64"), (3, 5, "fp64"), (2, 9, "fp32")])
 def test_kershaw_solve_reaches_uniform_mesh(p, nq, prec):
     """The Kershaw mesh (sliding boundary) solved on the GPU ends at the
@@ -289,8 +329,8 @@ def test_limiting_term_parity(case, precision):
     y_o, ya = O.hessian_apply(om, m.x, v, with_abs=True)
     rd = torch.float32 if precision == "fp32" else torch.float64
     assert_vec_close(host(gm.hessian_apply(dev(v, rd))), y_o, ya, tol=tol, what="apply + limiting")
-    dg_o = O.hessian_diag(om, m.x)
-    assert_vec_close(host(gm.hessian_diag()), dg_o, np.abs(dg_o), tol=tol, what="diag + limiting")
+    dg_o, dga = O.hessian_diag(om, m.x, with_abs=True)
+    assert_vec_close(host(gm.hessian_diag()), dg_o, dga, tol=tol, what="diag + limiting")
     if precision != "fp32":
         # a fixed number of MINRES iterations on both sides (no stop-test tie)
         xo = m.x.copy()
