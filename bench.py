@@ -37,16 +37,32 @@ METRIC = "Hessian-apply GDOF/s & %HBM peak (3D hex p=2..4); time-to-converged-me
 UNIT = "GDOF/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 rate (profiling recipe table)
 MINRES_ITS = 20
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_apply launch, captured on the
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one action launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {"fp64": 2.780e9, "fp32": 1.394e9}
+TRAFFIC_BYTES = {"fp64": 2.693e9, "fp32": 1.368e9}     # variants 5 (fp64 class) and 4 (fp32)
+PRECISION_LABEL = {"fp64": "fp64-class (double-float contractions, 48-bit significand)",
+                   "fp32": "fp32-mixed (fp32 stored d2mu/dT2, action and MINRES; fp64 residual, "
+                           "energy, det and line search)",
+                   "fp64-native": "fp64 (every contraction on the FP64 units)"}
+APPLY_VARIANT_NAME = {0: "sum-factorised register column", 1: "collocated, register column, 4 warps/CTA",
+                      2: "collocated, register column, 2 warps/CTA",
+                      3: "collocated, shared-memory column, 4 warps/CTA",
+                      4: "collocated, shared-memory column, 2 warps/CTA",
+                      5: "collocated, shared-memory column, 8 warps/CTA",
+                      6: "collocated, shared-memory column unrolled, 4 warps/CTA"}
 
 
-def flops_apply_per_elem(d, ni, nq, ns):
-    """Algorithmic flops of one element of the Hessian action: sum-factorised
-    forward and transposed contractions (2 flops per multiply-add) plus the
-    pointwise H:dA with the full d^2 x d^2 matrix."""
+def flops_apply_per_elem(d, ni, nq, ns, collocated=False):
+    """Algorithmic flops of one element of the Hessian action: forward and
+    transposed contractions (2 flops per multiply-add) plus the pointwise
+    H:dA with the full d^2 x d^2 matrix.  Sum-factorised with B and G
+    (the count of the method's statement), or, for the collocated kernels,
+    three B contractions to the points and the collocated derivative along
+    each direction."""
+    if d == 3 and collocated:
+        fwd = nq * ni ** 3 + nq ** 2 * ni ** 2 + nq ** 3 * ni + 3 * nq ** 4
+        return 2 * (2 * d * fwd) + 2 * (d * d) ** 2 * nq ** 3
     if d == 3:
         fwd = 2 * nq * ni ** 3 + 3 * nq ** 2 * ni ** 2 + 3 * nq ** 3 * ni
         return 2 * (2 * d * fwd) + 2 * (d * d) ** 2 * nq ** 3
@@ -54,12 +70,11 @@ def flops_apply_per_elem(d, ni, nq, ns):
     return 2 * (2 * d * fwd) + 2 * (d * d) ** 2 * nq ** 2
 
 
-def bytes_apply_per_elem(d, ni, nq, ns, rsz):
-    """Algorithmic bytes of one element of the Hessian action: the stored
-    quadrature data (ns values per point), the map, the gathered input and the
-    element-vector output (d (p+1)^d values each)."""
-    np_, nqd = ni ** d, nq ** d
-    return ns * nqd * rsz + np_ * 4 + 2 * d * np_ * rsz
+def bytes_apply(E, ndof, d, ni, nq, ns, rsz):
+    """Algorithmic bytes of one Hessian action: the stored quadrature data (ns
+    values per point) and the element map of every element, plus the input v
+    read and the result y written once per unique DOF (rsz bytes a value)."""
+    return E * (ns * nq ** d * rsz + ni ** d * 4) + 2 * ndof * rsz
 
 
 class Clocks:
@@ -220,8 +235,13 @@ def run_ours(args, rank, world, local_rank):
     rsz = 4 if args.precision == "fp32" else 8
     E = m.num_elems
     apply_avg_ms = apply_ms / max(apply_n, 1)
-    flops = flops_apply_per_elem(d, ni, nq, ns) * E
-    byts = bytes_apply_per_elem(d, ni, nq, ns, rsz) * E
+    byts = bytes_apply(E, m.ndof, d, ni, nq, ns, rsz)
+    var = capi.tmop_get_apply_variant(d, p, nq, {"fp64": capi.FP64, "fp32": capi.FP32,
+                                                 "fp64-native": capi.FP64_NATIVE}[args.precision])
+    flops = flops_apply_per_elem(d, ni, nq, ns, collocated=var > 0) * E
+    rc_name = {"fp64": "double,df", "fp32": "float,float", "fp64-native": "double,double"}[args.precision]
+    kname = (f"k_apply3c<Cfg<{d},{p},{nq}>,{rc_name},...> variant {var} ({APPLY_VARIANT_NAME[var]})"
+             if var > 0 else f"k_apply3<Cfg<{d},{p},{nq}>,{rc_name}> variant 0")
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     gbs = byts / (apply_avg_ms * 1e-3) / 1e9
@@ -230,15 +250,14 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": args.traffic,
                 "peak_source": "nominal FP64 rate of the profiling recipe",
-                "kernel": "k_apply<Cfg<3,3,4>,double,double>", "flops_per_launch": flops,
+                "kernel": kname, "flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm,
                              "frac": (gbs / hbm) if hbm else None, "bytes_per_launch": byts}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (gbs / hbm) if hbm else None, "traffic": args.traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "kernel": ("k_apply<Cfg<3,3,4>,float,float>" if args.precision == "fp32"
-                           else "k_apply<Cfg<3,3,4>,double,df> (double-float)"),
+                "kernel": kname,
                 "bytes_per_launch": byts,
                 "flops_view": {"fp64_equiv_tflops": flops / (apply_avg_ms * 1e-3) / 1e12}}
     roof["avg_launch_ms"] = apply_avg_ms
@@ -252,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic seeded perturbed Cartesian mesh (no dataset)",
         "config": {"workload": f"3D hex {m.n[0]}^3 Q{p}, {nq}^3 Gauss pts, mu_303, identity target, "
                                f"1 Newton step = energy+grad+PA setup+diag+{MINRES_ITS} MINRES+line search",
-                   "dofs": m.ndof, "elements": E, "precision": args.precision,
+                   "dofs": m.ndof, "elements": E, "precision": PRECISION_LABEL[args.precision],
                    "hessian_applies_per_step": applies,
                    "l2": "inputs larger than L2 (stored d2mu/dT2 "
                          f"{ns * nq ** d * E * rsz / 1e9:.2f} GB), no flush",
@@ -279,27 +298,99 @@ def run_ours(args, rank, world, local_rank):
             out["variants"][prec] = {"value": v["value"], "ms_per_step": v["ms_per_step"],
                                      "dtype": v["dtype"], "roofline": v["roofline"],
                                      "kernel_ms": v["kernel_ms"]}
+    if rank == 0 and not args.no_ttc and not args.no_cpu_baseline:
+        out["time_to_converged"] = time_to_converged(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
 
 
-def cpu_baseline(args, seconds=None):
-    """The FP64 oracle as it stands (single thread), one Newton step with
-    exactly 20 MINRES iterations on a bounded sample of the workload: the same
-    mesh family at 8^3 elements (1/216 of the 48^3 elements)."""
+def _oracle_step(n_s, order, seed):
+    """One oracle Newton step (exactly 20 MINRES iterations) on an n_s^3 mesh
+    of the benchmark family: (DOFs, seconds, status).  Runs in a worker."""
     import oracle as O
     from paper_2205_12721_b300 import meshgen
-    n_s = args.cpu_sample_n
-    m = meshgen.config_mesh(3, n_e=n_s, order=args.order)
+    m = meshgen.config_mesh(3, n_e=n_s, order=order, seed=seed)
     om = O.Mesh(3, m.order, m.order + 1, m.map, m.num_nodes, 303, m.fixed)
     x = m.x.copy()
     t0 = time.perf_counter()
     r = O.newton_step(om, x, 0.0, MINRES_ITS, True)
-    dt = time.perf_counter() - t0
-    return {"value": m.ndof * MINRES_ITS / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle Newton step (20 MINRES) on the {n_s}^3 Q{m.order} mesh of the "
-                      f"same family ({m.ndof} DOFs), {dt:.2f} s", "status": r["status"]}
+    return m.ndof, time.perf_counter() - t0, r["status"]
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(args, seconds=None):
+    """The FP64 oracle as it stands, one Newton step with exactly 20 MINRES
+    iterations on a bounded sample of the workload: the same mesh family at
+    8^3 elements (1/216 of the 48^3 elements).  Timed single-threaded, and on
+    all host cores as one independent oracle process per core, each on the
+    same sample (the oracle is single-threaded; the cores share no work);
+    value = the all-core throughput.""" 
+    import multiprocessing as mp
+    n_s, order = args.cpu_sample_n, args.order
+    ndof, dt1, st = _oracle_step(n_s, order, None)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.starmap(_oracle_step, [(2, order, 1)] * cores)          # start-up, imports
+        t0 = time.perf_counter()
+        res = pool.starmap(_oracle_step, [(n_s, order, None)] * cores)
+        wall = time.perf_counter() - t0
+    tot = sum(r[0] for r in res) * MINRES_ITS
+    return {"value": tot / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(), "nproc": cores,
+            "single_thread": {"value": ndof * MINRES_ITS / dt1 / 1e9, "cores": 1, "seconds": dt1},
+            "sample": f"one oracle Newton step (20 MINRES) per core on the {n_s}^3 Q{order} mesh of the "
+                      f"same family ({ndof} DOFs), {cores} independent processes, {wall:.2f} s "
+                      f"wall; single thread {dt1:.2f} s",
+            "status": max([st] + [r[2] for r in res])}
+
+
+def time_to_converged(args, reps=5):
+    """Time to converged mesh of the 3D 24^3 Q2 mu_302 configuration (smooth +
+    noise perturbation, |dF|/|dF0| <= 1e-10, MINRES rtol 1e-8 / cap 50),
+    FP64 class vs FP32 mixed: p50 / p99 over repeated solves from the same
+    initial mesh, Newton and MINRES counts, and the final-energy difference."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    m = meshgen.config_mesh(2)
+    out = {"workload": "3D hex 24^3 Q2, 3^3 Gauss pts, mu_302, identity target, until "
+                       "|dF|/|dF0| <= 1e-10", "dofs": m.ndof, "unit": "s"}
+    finals = {}
+    for prec in ("fp64", "fp32"):
+        times = []
+        for rep in range(reps + 1):                       # the first solve warms up
+            gm = TmopMesh.from_structured(m, capi.METRIC_302, precision=prec)
+            x = torch.from_numpy(m.x).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps_ = gm.solve(x, max_newton=100, rtol=1e-10)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st, F, _ = gm.energy(x)
+            S = float(m.num_elems)                        # sum_q |c_q| for W = I on [0,1]^3
+            gm.close()
+            if rep:
+                times.append(dt)
+        finals[prec] = F
+        ts = sorted(times)
+        out[prec] = {"p50_s": statistics.median(ts), "p99_s": ts[-1], "runs": len(ts),
+                     "newton_its": len(reps_), "minres_its": sum(r["minres_iters"] for r in reps_),
+                     "status": reps_[-1]["status"], "energy_final": F}
+    out["fp32_vs_fp64_final_energy_abs"] = abs(finals["fp32"] - finals["fp64"])
+    out["final_energy_tol"] = 1e-8 * S
+    return out
 
 
 def run_reference(args, rank, world):
@@ -443,7 +534,7 @@ def run_sweep(args):
                     ams, _ = capi.tmop_profile_read(gm.ctx, capi.K_ASSEMBLE)
                     gm.close()
                     t = ms / nl
-                    byts = bytes_apply_per_elem(3, p + 1, nq, 45, rsz) * m.num_elems
+                    byts = bytes_apply(m.num_elems, m.ndof, 3, p + 1, nq, 45, rsz)
                     rows.append({"precision": prec, "p": p, "nq": nq, "n_e": n, "dofs": m.ndof,
                                  "apply_ms": t, "assemble_ms": ams / nl,
                                  "gdofs_kernel": m.ndof / (t * 1e-3) / 1e9,
@@ -621,6 +712,45 @@ def run_serving(args):
             "by_rate": res}
 
 
+def run_autotune(args):
+    """The autotuner over the Hessian-action kernel variants: for every
+    configuration with more than one variant (3D, p = 1..4, n_q = p+1 and p+2
+    with n_q^2 <= 32) and every precision, a mesh of the benchmark family whose
+    stored data exceeds L2 (~1.2 GB), tmop_autotune (CUDA events, 10 launches
+    per variant); prints the measured times and the chosen variant per
+    configuration, the rows of autotune_table.json."""
+    import torch
+    from paper_2205_12721_b300 import capi, meshgen
+    from paper_2205_12721_b300.mesh_opt import TmopMesh
+    hbm = measured_peaks().get("hbm_gbs")
+    precs = {"fp64": capi.FP64, "fp32": capi.FP32, "fp64-native": capi.FP64_NATIVE}
+    rows = []
+    for p in (1, 2, 3, 4):
+        for nq in (p + 1, p + 2):
+            if capi.tmop_apply_variants(3, p, nq) <= 1:
+                continue
+            for name in args.autotune_precisions:
+                rsz = 4 if name == "fp32" else 8
+                per_el = 45 * nq ** 3 * rsz
+                n = max(8, int(round((args.autotune_bytes / per_el) ** (1.0 / 3.0))))
+                m = meshgen.config_mesh(3, n_e=n, order=p)
+                gm = TmopMesh.from_structured(m, capi.METRIC_303, nq1d=nq, precision=name)
+                x = torch.from_numpy(m.x).cuda()
+                gm.hessian_setup(x)
+                best, ms = capi.tmop_autotune(gm.ctx, 10)
+                gm.close()
+                byts = bytes_apply(m.num_elems, m.ndof, 3, p + 1, nq, 45, rsz)
+                rows.append({"d": 3, "p": p, "nq": nq, "precision": name, "prec": precs[name],
+                             "n_e": n, "dofs": m.ndof, "variant": best,
+                             "ms": [round(t, 5) for t in ms],
+                             "hbm_frac_best": (byts / (min(ms) * 1e-3) / 1e9 / hbm) if hbm else None,
+                             "gdofs_best": m.ndof / (min(ms) * 1e-3) / 1e9})
+                del x
+                torch.cuda.empty_cache()
+    return {"metric": "Hessian-action kernel variant per configuration (autotuner)",
+            "unit": "ms", "higher_is_better": False, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,10 +762,12 @@ def main():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--cpu-sample-n", dest="cpu_sample_n", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", nargs="*", default=["fp32"],
+    ap.add_argument("--no-ttc", action="store_true", help="skip the 24^3 Q2 time-to-converged leg")
+    ap.add_argument("--variants", nargs="*", default=["fp32", "fp64-native"],
                     help="other precisions timed after the main run (rank 0)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "batched", "serving", "sweep", "solve", "kershaw", "remap"])
+                    choices=["newton", "batched", "serving", "sweep", "solve", "kershaw", "remap",
+                             "autotune"])
     ap.add_argument("--kershaw-orders", dest="kershaw_orders", type=int, nargs="+", default=[1, 2, 3, 4])
     ap.add_argument("--kershaw-precisions", dest="kershaw_precisions", nargs="+",
                     default=["fp64", "fp32"])
@@ -654,6 +786,9 @@ def main():
     ap.add_argument("--n2", type=int, nargs=2, default=[8, 128])
     ap.add_argument("--n3", type=int, nargs=2, default=[4, 40])
     ap.add_argument("--budget-gb", dest="budget_gb", type=float, default=64.0)
+    ap.add_argument("--autotune-precisions", dest="autotune_precisions", nargs="+",
+                    default=["fp64", "fp32", "fp64-native"])
+    ap.add_argument("--autotune-bytes", dest="autotune_bytes", type=float, default=1.2e9)
     ap.add_argument("--traffic", type=float, default=None,
                     help="override the ncu dram bytes per launch of the apply kernel")
     args = ap.parse_args()
@@ -664,7 +799,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.workload != "newton":
         out = {"batched": run_batched, "serving": run_serving, "sweep": run_sweep,
-               "solve": run_solve, "kershaw": run_kershaw, "remap": run_remap}[args.workload](args)
+               "solve": run_solve, "kershaw": run_kershaw, "remap": run_remap,
+               "autotune": run_autotune}[args.workload](args)
         if rank == 0:
             print(json.dumps(out))
         return

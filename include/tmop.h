@@ -392,6 +392,38 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int kernel_class, double *total_ms,
 /* Bytes of device memory the context holds. */
 int64_t tmop_device_bytes(const tmop_ctx *ctx);
 
+/* ---- Kernel-variant autotuning (not part of the paper's method) ----------
+ * The Hessian action (the dominant kernel, Sec. 3.4) has several kernel
+ * variants for some configurations (3D with nq1d^2 <= 32): the
+ * sum-factorised kernel (variant 0) and collocated-derivative kernels that
+ * keep the per-point values in registers or shared memory, with 2, 4 or 8
+ * warps per CTA.  All compute the same action.  A process-wide table gives
+ * the variant per (dim, order, nq1d, precision); its defaults were measured
+ * on a B300 by the autotuner, and every context and batch of the process
+ * uses it at each launch.  Changing an entry while another host thread
+ * launches actions of that configuration is allowed (the entry is atomic);
+ * a launch uses the value it reads. */
+
+/* Number of action variants of a configuration (1 = only variant 0; 0 =
+ * unsupported configuration). */
+int tmop_apply_variants(int dim, int order, int nq1d);
+
+/* The variant in use for (dim, order, nq1d, precision), and its override
+ * (variant -1 restores the measured default).  TMOP_ERR_ARG for an
+ * unsupported configuration or a variant out of range. */
+tmop_status tmop_get_apply_variant(int dim, int order, int nq1d, int precision, int *variant);
+tmop_status tmop_set_apply_variant(int dim, int order, int nq1d, int precision, int variant);
+
+/* Time every action variant on this context's own mesh and stored data
+ * (reps launches each after one warm-up, CUDA events on the context's
+ * stream, input vector zero), install the fastest in the process-wide table
+ * and return it.  Requires a previous tmop_hessian_setup.
+ *   variant  host (may be NULL): the chosen variant.
+ *   ms       host (may be NULL): tmop_apply_variants(...) entries, the mean
+ *            time of one launch of each variant.
+ * Synchronises; overwrites the context's internal work vectors. */
+tmop_status tmop_autotune(tmop_ctx *ctx, int reps, int *variant, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,9 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
            "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
            "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference",
-           "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det")
+           "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det",
+           "tmop_apply_variants", "tmop_get_apply_variant", "tmop_set_apply_variant",
+           "tmop_autotune")
 
 
 class TmopError(RuntimeError):
@@ -113,6 +115,10 @@ def lib():
             "tmop_energy": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "tmop_gradient": (I, [P, P, P]),
             "tmop_det": (I, [P, P, P]),
+            "tmop_apply_variants": (I, [I, I, I]),
+            "tmop_get_apply_variant": (I, [I, I, I, I, ctypes.POINTER(I)]),
+            "tmop_set_apply_variant": (I, [I, I, I, I, I]),
+            "tmop_autotune": (I, [P, I, ctypes.POINTER(I), P]),
             "tmop_hessian_setup": (I, [P, P]),
             "tmop_hessian_apply": (I, [P, P, P]),
             "tmop_hessian_diag": (I, [P, P]),
@@ -193,6 +199,33 @@ def tmop_energy(ctx: int, x, check: bool = True):
     if check and st not in (OK, ERR_INVERTED):
         _check(st, "tmop_energy")
     return st, F.value, md.value
+
+
+def tmop_apply_variants(dim: int, order: int, nq1d: int) -> int:
+    return int(lib().tmop_apply_variants(dim, order, nq1d))
+
+
+def tmop_get_apply_variant(dim: int, order: int, nq1d: int, precision: int) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().tmop_get_apply_variant(dim, order, nq1d, precision, ctypes.byref(v)),
+           "tmop_get_apply_variant")
+    return v.value
+
+
+def tmop_set_apply_variant(dim: int, order: int, nq1d: int, precision: int, variant: int):
+    _check(lib().tmop_set_apply_variant(dim, order, nq1d, precision, variant),
+           "tmop_set_apply_variant")
+
+
+def tmop_autotune(ctx: int, reps: int = 10):
+    """(chosen variant, [ms per launch of variant 0, 1, ...])."""
+    v = ctypes.c_int(0)
+    ms = (ctypes.c_double * 16)(*([float("nan")] * 16))
+    _check(lib().tmop_autotune(ctx, reps, ctypes.byref(v), ms), "tmop_autotune")
+    times = [float(t) for t in ms]
+    while times and times[-1] != times[-1]:      # drop the unused (NaN) slots
+        times.pop()
+    return v.value, times
 
 
 def tmop_det(ctx: int, x, det):

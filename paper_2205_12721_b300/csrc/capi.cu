@@ -987,4 +987,67 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int cls, double *total_ms, int64_t 
 
 int64_t tmop_device_bytes(const tmop_ctx *ctx) { return ctx ? ctx->bytes : 0; }
 
+int tmop_apply_variants(int dim, int order, int nq1d)
+{
+    if (!elem_supported(dim, order, nq1d)) return 0;
+    return apply_variant_count(dim, order, nq1d);
+}
+
+tmop_status tmop_get_apply_variant(int dim, int order, int nq1d, int precision, int *variant)
+{
+    if (!variant || !elem_supported(dim, order, nq1d) || precision < 0 || precision > 2)
+        return fail(TMOP_ERR_ARG, "bad configuration, precision or NULL output");
+    *variant = apply_variant(dim, order, nq1d, precision);
+    return TMOP_OK;
+}
+
+tmop_status tmop_set_apply_variant(int dim, int order, int nq1d, int precision, int variant)
+{
+    if (!elem_supported(dim, order, nq1d) || !set_apply_variant(dim, order, nq1d, precision, variant))
+        return fail(TMOP_ERR_ARG, "bad configuration, precision or variant");
+    return TMOP_OK;
+}
+
+tmop_status tmop_autotune(tmop_ctx *c, int reps, int *variant, double *ms)
+{
+    if (!c || reps < 1) return fail(TMOP_ERR_ARG, "NULL context or reps < 1");
+    if (!c->h_ready) return fail(TMOP_ERR_ARG, "tmop_hessian_setup has not been called");
+    const int n = apply_variant_count(c->d, c->p, c->nq);
+    const ElemParams P = c->params();
+    CK(cudaMemsetAsync(c->vm, 0, c->rsz * (size_t)c->ndof, c->stream));
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) { cudaEventDestroy(a); return cuda_fail(e, "cudaEventCreate"); }
+    int best = -1;
+    double best_ms = 0.0;
+    for (int v = 0; v < n && e == cudaSuccess; ++v) {
+        set_apply_variant(c->d, c->p, c->nq, c->prec, v);
+        auto launch = [&] {
+            return launch_apply(c->d, c->p, c->nq, P, c->vm, c->H, c->evR, c->prec, nullptr, 0,
+                                c->stream);
+        };
+        if ((e = launch()) != cudaSuccess) break;             // warm-up (and kernel attributes)
+        if ((e = cudaEventRecord(a, c->stream)) != cudaSuccess) break;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e != cudaSuccess || (e = cudaEventRecord(b, c->stream)) != cudaSuccess ||
+            (e = cudaEventSynchronize(b)) != cudaSuccess)
+            break;
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, a, b)) != cudaSuccess) break;
+        const double per = (double)t / reps;
+        if (ms) ms[v] = per;
+        if (best < 0 || per < best_ms) {
+            best = v;
+            best_ms = per;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_apply_variant(c->d, c->p, c->nq, c->prec, e == cudaSuccess ? best : -1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    if (variant) *variant = best;
+    return TMOP_OK;
+}
+
 }  // extern "C"

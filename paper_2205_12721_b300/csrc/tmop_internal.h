@@ -42,6 +42,11 @@ cudaError_t launch_hsetup(int d, int p, int q, const ElemParams &P, const double
 cudaError_t launch_apply(int d, int p, int q, const ElemParams &P, const void *v, const void *H,
                          void *ev, int prec, const int *stop_iter, int k, cudaStream_t s,
                          const BatchArgs *B = nullptr, int64_t ntiles = 0);
+// Action kernel variants (elem_apply_impl.cuh): count for a configuration,
+// the one in use for (config, precision), and its override (-1 = table default).
+int apply_variant_count(int d, int p, int q);
+int apply_variant(int d, int p, int q, int prec);
+bool set_apply_variant(int d, int p, int q, int prec, int variant);
 cudaError_t launch_diag(int d, int p, int q, const ElemParams &P, const void *H, void *ev, int prec,
                         cudaStream_t s, const BatchArgs *B = nullptr, int64_t ntiles = 0);
 
