@@ -214,26 +214,29 @@ tmop_status tmop_det(tmop_ctx *ctx, const double *x, double *det);
  * claimed the device memory, or latency-bound loops where cudaMalloc/cudaFree
  * would synchronise the device).  It computes what tmop_energy computes, with
  * no context: the per-CTA partial sums and the 1D basis tables live in one
- * file-scope device array of 1 MiB (65,536 partial pairs + 2 x 128 table
- * values), which every GPU that loads the library holds until the process
- * exits.
+ * file-scope device array of about 1 MiB (65,536 partial pairs + the tables of
+ * every supported (order, nq1d)), which every GPU that loads the library
+ * holds until the process exits.
  *   desc          host; sizes, metric and target as for tmop_setup;
- *                 hess_precision selects the contraction arithmetic as there.
+ *                 hess_precision selects the contraction arithmetic as there
+ *                 (TMOP_FP64_NATIVE: FP64 units; otherwise double-float).
  *   elem_to_node  device int32, num_elems * (order+1)^dim, in range (not checked).
  *   x             device FP64, dim * num_nodes.
  *   out           device FP64[2]; receives F(x) and min det(A).  F is the sum
  *                 over points with det A > 0: check out[1] > 0 (otherwise the
  *                 mesh is inverted and F is meaningless).
- *   cuda_stream   stream for the copy and the two launches.
+ *   cuda_stream   stream of the two launches.
  * Meshes needing more than 65,536 CTAs (e.g. more than 524,288 elements for
- * 3D p = 3 with 4^3 points) are rejected with TMOP_ERR_ARG; use tmop_energy.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
- * every value a call reads is written by that call, so nothing is cleared.
- * Calls that overlap on the GPU (different streams, or different host
- * threads) race on the array.  Asynchronous; never calls cudaMalloc,
- * cudaFree or any allocating routine. */
+ * 3D p = 3 with 4^3 points) are rejected with TMOP_ERR_ARG before anything
+ * is launched; use tmop_energy.  The first call on a device looks up the
+ * array's device address and writes the tables into it with one synchronous
+ * copy (once per device, with that device current); make that first call
+ * before any stream capture.  Every later call is asynchronous: two kernel
+ * launches on cuda_stream, no copy.  All calls share the array and it keeps
+ * the last call's partial sums; every value a call reads is written by that
+ * call (or is a table), so nothing is cleared.  Calls that overlap on the
+ * GPU (different streams, or different host threads) race on the partial
+ * sums.  Never calls cudaMalloc, cudaFree or any allocating routine. */
 tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t *elem_to_node,
                                 const double *x, double *out, void *cuda_stream);
 
@@ -391,6 +394,21 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int kernel_class, double *total_ms,
 
 /* Bytes of device memory the context holds. */
 int64_t tmop_device_bytes(const tmop_ctx *ctx);
+
+/* ---- Fault injection for the tests of the failure paths (host side) -----
+ * No GPU fault is involved: the library pretends, on the host, that a
+ * computation failed, and the tests check what the caller then sees. */
+enum { TMOP_FAULT_NONE = 0, TMOP_FAULT_MINRES_BREAKDOWN = 1 };
+
+/* The next Newton step of the context (tmop_inject_fault) or of one mesh of
+ * a batch (tmop_batch_inject_fault) treats its MINRES solve, after running
+ * it, as broken down (as if a preconditioned inner product had been negative
+ * or not finite, which valid inputs never produce with M^-1 = 1/|diag|): the
+ * step returns TMOP_ERR_MINRES with x unchanged; the batch mesh is retired
+ * with that status, the other meshes are not affected.  Applies once;
+ * TMOP_FAULT_NONE cancels.  TMOP_ERR_ARG for an unknown fault or slot. */
+tmop_status tmop_inject_fault(tmop_ctx *ctx, int fault);
+tmop_status tmop_batch_inject_fault(tmop_batch *b, int slot, int fault);
 
 /* ---- Kernel-variant autotuning (not part of the paper's method) ----------
  * The Hessian action (the dominant kernel, Sec. 3.4) has several kernel

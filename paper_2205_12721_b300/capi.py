@@ -33,7 +33,7 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference",
            "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det",
            "tmop_apply_variants", "tmop_get_apply_variant", "tmop_set_apply_variant",
-           "tmop_autotune")
+           "tmop_autotune", "tmop_inject_fault", "tmop_batch_inject_fault")
 
 
 class TmopError(RuntimeError):
@@ -119,6 +119,8 @@ def lib():
             "tmop_get_apply_variant": (I, [I, I, I, I, ctypes.POINTER(I)]),
             "tmop_set_apply_variant": (I, [I, I, I, I, I]),
             "tmop_autotune": (I, [P, I, ctypes.POINTER(I), P]),
+            "tmop_inject_fault": (I, [P, I]),
+            "tmop_batch_inject_fault": (I, [P, I, I]),
             "tmop_hessian_setup": (I, [P, P]),
             "tmop_hessian_apply": (I, [P, P, P]),
             "tmop_hessian_diag": (I, [P, P]),
@@ -226,6 +228,17 @@ def tmop_autotune(ctx: int, reps: int = 10):
     while times and times[-1] != times[-1]:      # drop the unused (NaN) slots
         times.pop()
     return v.value, times
+
+
+FAULT_NONE, FAULT_MINRES_BREAKDOWN = 0, 1
+
+
+def tmop_inject_fault(ctx: int, fault: int):
+    _check(lib().tmop_inject_fault(ctx, fault), "tmop_inject_fault")
+
+
+def tmop_batch_inject_fault(b: int, slot: int, fault: int):
+    _check(lib().tmop_batch_inject_fault(b, slot, fault), "tmop_batch_inject_fault")
 
 
 def tmop_det(ctx: int, x, det):

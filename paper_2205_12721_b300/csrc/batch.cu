@@ -456,6 +456,7 @@ struct tmop_batch {
     size_t hbuf_cap = 0;
     int nt_e = 0, nt_n = 0, nt_v = 0, nm = 0;
     int64_t bytes = 0;
+    std::vector<int> fault;              // host-side fault of a mesh's next step (tests)
 };
 
 namespace {
@@ -739,6 +740,7 @@ tmop_status tmop_batch_create(const tmop_batch_desc *desc, void *cuda_stream, tm
     b->slab.assign(D.max_meshes, nullptr);
     b->slab_bytes.assign(D.max_meshes, 0);
     b->used.assign(D.max_meshes, 0);
+    b->fault.assign(D.max_meshes, TMOP_FAULT_NONE);
     auto bail = [&](tmop_status st) {
         tmop_batch_destroy(b);
         return st;
@@ -853,6 +855,7 @@ tmop_status tmop_batch_add(tmop_batch *b, int64_t num_elems, int64_t num_nodes,
     b->hM[slot] = M;
     b->hS[slot] = S0;
     b->used[slot] = 1;
+    b->fault[slot] = TMOP_FAULT_NONE;
     *slot_out = slot;
     return TMOP_OK;
 }
@@ -899,8 +902,24 @@ tmop_status tmop_batch_step(tmop_batch *b, int *n_active)
         if ((st = set_subset(b, work)) != TMOP_OK) return st;
         st = (b->vprec == TMOP_FP32) ? setup_and_minres<float>(b) : setup_and_minres<double>(b);
         if (st != TMOP_OK) return st;
-        st = (b->vprec == TMOP_FP32) ? line_search<float>(b, work) : line_search<double>(b, work);
-        if (st != TMOP_OK) return st;
+        if ((st = read_states(b)) != TMOP_OK) return st;
+        // a mesh whose MINRES broke down takes no line search: its positions stay
+        // as they are and b_finish retires it with TMOP_ERR_MINRES
+        std::vector<int> search;
+        for (int m : work) {
+            if (b->fault[m] == TMOP_FAULT_MINRES_BREAKDOWN) {     // tmop_batch_inject_fault
+                b->fault[m] = TMOP_FAULT_NONE;
+                b->hS[m].ms.breakdown = 1;
+                BCK(cudaMemcpyAsync(&b->dS[m].ms.breakdown, &b->hS[m].ms.breakdown, sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream));
+            }
+            if (!b->hS[m].ms.breakdown) search.push_back(m);
+        }
+        if (!search.empty()) {
+            st = (b->vprec == TMOP_FP32) ? line_search<float>(b, search)
+                                         : line_search<double>(b, search);
+            if (st != TMOP_OK) return st;
+        }
         if ((st = set_subset(b, work)) != TMOP_OK) return st;
         b_finish<<<blocks_for(b->nm, 128), 128, 0, b->stream>>>(b->dS, b->dmlist, b->nm);
         count_launch();
@@ -911,6 +930,15 @@ tmop_status tmop_batch_step(tmop_batch *b, int *n_active)
     for (int m = 0; m < b->desc.max_meshes; ++m)
         if (b->used[m] && !b->hS[m].done) ++n;
     if (n_active) *n_active = n;
+    return TMOP_OK;
+}
+
+tmop_status tmop_batch_inject_fault(tmop_batch *b, int slot, int fault)
+{
+    if (!b || slot < 0 || slot >= b->desc.max_meshes || !b->used[slot] ||
+        (fault != TMOP_FAULT_NONE && fault != TMOP_FAULT_MINRES_BREAKDOWN))
+        return bfail(TMOP_ERR_ARG, "bad slot or unknown fault");
+    b->fault[slot] = fault;
     return TMOP_OK;
 }
 

@@ -94,10 +94,7 @@ struct tmop_ctx {
     // discrete target field and its remap (allocated on first use)
     double *eta = nullptr, *eta_t = nullptr;
     bool eta_set = false;
-    // fused energies from FP64 invariants once the Newton energy has fallen
-    // eight orders below the largest seen (a zero-energy optimum is near)
-    bool energy_fp64 = false;
-    double energy_ref = 0.0;
+    int fault = TMOP_FAULT_NONE;     // host-side fault of the next Newton step (tests)
     double *rsrc_x0 = nullptr, *rsrc_eta0 = nullptr;
     bool remap_on = false;
     tmop_remap_opts remap_opts{4, 1e-12, 200};
@@ -132,7 +129,6 @@ struct tmop_ctx {
         P.target = desc.target;
         P.h0 = desc.target_h0;
         P.eta = eta;
-        P.energy_fp64 = energy_fp64 ? 1 : 0;
         return P;
     }
 
@@ -841,13 +837,6 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         if (st != TMOP_OK) return finish(st);
     }
     st = energy_grad_sync(c, x, c->g, &F0, &md0);
-    if (st == TMOP_OK) {
-        c->energy_ref = std::max(c->energy_ref, std::fabs(F0));
-        if (!c->energy_fp64 && std::fabs(F0) < 1e-8 * c->energy_ref) {
-            c->energy_fp64 = true;                      // from here on, and for this x too
-            st = energy_grad_sync(c, x, c->g, &F0, &md0);
-        }
-    }
     r.energy = F0;
     r.min_det = md0;
     if (st != TMOP_OK) return finish(st);
@@ -872,7 +861,13 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
     if (st != TMOP_OK) return finish(st);
     r.minres_iters = its;
     r.minres_resid = res;
-    if (brk) return finish(fail(TMOP_ERR_MINRES, "MINRES breakdown (preconditioner not positive)"));
+    if (c->fault == TMOP_FAULT_MINRES_BREAKDOWN) {          // injected by tmop_inject_fault
+        c->fault = TMOP_FAULT_NONE;
+        brk = 1;
+    }
+    if (brk)
+        return finish(fail(TMOP_ERR_MINRES, "MINRES breakdown (a preconditioned inner product was "
+                                            "negative or not finite)"));
     double alpha = 1.0;
     for (int h = 0; h <= o.ls_max_halvings; ++h, alpha *= 0.5) {
         cudaError_t e = launch_trial(x, c->dx, alpha, c->ndof, c->xt, c->stream);
@@ -986,6 +981,14 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int cls, double *total_ms, int64_t 
 }
 
 int64_t tmop_device_bytes(const tmop_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+
+tmop_status tmop_inject_fault(tmop_ctx *ctx, int fault)
+{
+    if (!ctx || (fault != TMOP_FAULT_NONE && fault != TMOP_FAULT_MINRES_BREAKDOWN))
+        return fail(TMOP_ERR_ARG, "NULL context or unknown fault");
+    ctx->fault = fault;
+    return TMOP_OK;
+}
 
 int tmop_apply_variants(int dim, int order, int nq1d)
 {

@@ -289,6 +289,15 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
 }
 
 // ---------------------------------------------------------------- gradient
+// The fused energy takes mu at a point from the double-float invariants
+// unless |mu| is below this bound: an error in I1 or tau enters mu at first
+// order, ~4e-15 on the scale 1 of the metrics' "- 1" (or (tau - 1)^2), so
+// near a zero-energy optimum (every |mu| small) the sum would stop at that
+// floor and the line search's F(x+) < 1.2 F(x) test would compare noise; there
+// the point's mu is recomputed from FP64 invariants of the same T.  The
+// decision is per point and per call: a result depends only on x.
+constexpr double kMuFp64Below = 1e-6;
+
 template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
 k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, double *part,
@@ -334,27 +343,26 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
                 }
                 const double sc = cq * iws;
                 df a, b;
-                const bool e64 = part && P.energy_fp64;
-                if (e64) {                         // energy from FP64 invariants
-                    double Tdb[C::DD];
-#pragma unroll
-                    for (int r = 0; r < C::DD; ++r) Tdb[r] = to_db(Td[r]);
-                    esum += cq * metric_mu_fp64<C::D>(P.metric, Tdb);
-                }
+                double mu_pt;
                 if (P.metric == MET_303 || P.metric == MET_303_55) {   // scalars in double-float too
                     InvW w;
-                    const df mu = metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
-                    if (!e64) esum += cq * to_db(mu);
+                    mu_pt = to_db(metric303_dw(I1w, tauw, P.metric == MET_303_55, w));
                     const df scw = from_db<df>(sc);
                     a = dw_mul(scw, df(2.0f * w.f1.h, 2.0f * w.f1.l));
                     b = dw_mul(scw, w.ft);
                 } else {
                     Inv v;
-                    const double mu = metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
-                    if (!e64) esum += cq * mu;
+                    mu_pt = metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
                     a = from_db<df>(2.0 * v.f1 * sc);
                     b = from_db<df>(v.ft * sc);
                 }
+                if (part && fabs(mu_pt) < kMuFp64Below) {
+                    double Tdb[C::DD];             // energy from FP64 invariants
+#pragma unroll
+                    for (int r = 0; r < C::DD; ++r) Tdb[r] = to_db(Td[r]);
+                    mu_pt = metric_mu_fp64<C::D>(P.metric, Tdb);
+                }
+                esum += cq * mu_pt;
 #pragma unroll
                 for (int r = 0; r < C::DD; ++r) {
                     df acc(0.0f, 0.0f);
@@ -378,8 +386,8 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
                     const double I2 = i2_dw(Td, Cd, I1w, g2, TtT, TTt);
                     Inv v;
                     const double mu = metric_scalars<3>(P.metric, I1, tau, I2, v);
-                    if (part && P.energy_fp64) {   // energy from FP64 invariants
-                        double Tdb[9];
+                    if (part && fabs(mu) < kMuFp64Below) {
+                        double Tdb[9];             // energy from FP64 invariants
 #pragma unroll
                         for (int r = 0; r < 9; ++r) Tdb[r] = to_db(Td[r]);
                         esum += cq * metric_mu_fp64<3>(P.metric, Tdb);

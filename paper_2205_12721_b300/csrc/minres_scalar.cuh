@@ -38,7 +38,7 @@ __device__ __forceinline__ void minres_beta_scalars(MinresState *st, double bb, 
                                                     int fixed_its)
 {
     st->iters = k;
-    if (bb < 0.0) {                  // M^-1 not positive: cannot happen with |diag|
+    if (!(bb >= 0.0)) {              // negative (M^-1 not positive) or not finite
         st->breakdown = 1;
         st->stop_iter = k - 1;       // discard this iteration
         return;

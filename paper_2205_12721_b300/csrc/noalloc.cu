@@ -14,12 +14,16 @@ namespace {
 
 constexpr int kMaxCtas = 65536;                   // partial (sum, min) pairs
 constexpr int kTableOffset = 2 * kMaxCtas;        // 1D tables follow the partials
-constexpr int kTableMax = 128;                    // >= 2 nq (p+1) + nq for p <= 4, nq <= 6
-// FP64 tables, then the same tables as double-float pairs (8 bytes each)
-constexpr int kScratchDoubles = kTableOffset + 2 * kTableMax;
+constexpr int kTableMax = 128;                    // B, G, w of one (p+1, nq) pair, FP64
+static_assert(2 * 9 * 5 + 9 <= kTableMax, "the 9-point rule at p = 4 must fit a table slot");
+// One slot per (p+1, nq) pair of the supported configurations: the FP64
+// tables, then the same values as double-float pairs (8 bytes each).
+constexpr int kSlots = 12;
+constexpr int kSlotDoubles = 2 * kTableMax;
+constexpr int kScratchDoubles = kTableOffset + kSlots * kSlotDoubles;
 
 // Shared by every call in the process on this device; holds the last call's
-// contents until the library is unloaded.
+// partial sums (and the tables, written once) until the library is unloaded.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -32,8 +36,20 @@ tmop_status set_error(tmop_status st, const std::string &m)
     return st;
 }
 
-// Device address of the scratch array for the current device (looked up once
-// per device; host code cannot use the symbol itself as a device pointer).
+// Table slot of a (p+1, nq) pair, -1 if none.
+int slot_of(int ni, int nq)
+{
+    static const int pairs[kSlots][2] = {{2, 2}, {2, 3}, {3, 3}, {3, 4}, {4, 4}, {4, 5},
+                                         {5, 5}, {5, 6}, {2, 9}, {3, 9}, {4, 9}, {5, 9}};
+    for (int i = 0; i < kSlots; ++i)
+        if (pairs[i][0] == ni && pairs[i][1] == nq) return i;
+    return -1;
+}
+
+// Device address of the scratch array for the current device.  The first
+// call on a device looks it up (host code cannot use the symbol itself as a
+// device pointer) and writes the tables of every configuration into their
+// slots with one synchronous copy; later calls only read them.
 tmop_status scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -46,6 +62,20 @@ tmop_status scratch_for_current_device(double **out)
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess)
             return set_error(TMOP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        static double host[kSlots * kSlotDoubles];
+        for (int ni = 2; ni <= 5; ++ni)
+            for (int nq = 2; nq <= 9; ++nq) {
+                const int sl = slot_of(ni, nq);
+                if (sl < 0) continue;
+                double *tab = host + sl * kSlotDoubles;
+                tmop::host_basis_tables(ni, nq, tab, tab + nq * ni, tab + 2 * nq * ni);
+                tmop::df *tabw = reinterpret_cast<tmop::df *>(tab + kTableMax);
+                for (int i = 0; i < 2 * nq * ni + nq; ++i) tabw[i] = tmop::df(tab[i]);
+            }
+        e = cudaMemcpy(static_cast<double *>(p) + kTableOffset, host, sizeof(host),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return set_error(TMOP_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString(e));
         g_scratch_addr[dev] = static_cast<double *>(p);
     }
     *out = g_scratch_addr[dev];
@@ -74,43 +104,39 @@ extern "C" tmop_status tmop_energy_noalloc(const tmop_desc *desc, const int32_t 
     if (D.num_elems < 0 || D.num_nodes <= 0) return set_error(TMOP_ERR_ARG, "bad mesh sizes");
     if (D.limit_delta != 0.0)
         return set_error(TMOP_ERR_UNSUPPORTED, "the limiting term is not available without a context");
-    if (D.num_elems > 0 && !elem_to_node) return set_error(TMOP_ERR_ARG, "elem_to_node is NULL");
+    if (D.hess_precision != TMOP_FP64 && D.hess_precision != TMOP_FP32 &&
+        D.hess_precision != TMOP_FP64_NATIVE)
+        return set_error(TMOP_ERR_ARG, "hess_precision must be TMOP_FP64, TMOP_FP32 or TMOP_FP64_NATIVE");
     const int64_t nb = elem_blocks(D.dim, D.order, D.nq1d, D.num_elems);
     if (nb > kMaxCtas)
         return set_error(TMOP_ERR_ARG, "mesh too large for tmop_energy_noalloc: needs " +
                                            std::to_string(nb) + " CTAs, the static scratch holds " +
                                            std::to_string(kMaxCtas) + "; use tmop_energy");
+    if (D.num_elems > 0 && !elem_to_node) return set_error(TMOP_ERR_ARG, "elem_to_node is NULL");
+    const int sl = slot_of(D.order + 1, D.nq1d);
+    if (sl < 0) return set_error(TMOP_ERR_UNSUPPORTED, "no table slot for this (order, nq1d)");
 
     double *scratch = nullptr;
     tmop_status st = scratch_for_current_device(&scratch);
     if (st != TMOP_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
-    // 1D tables on the host stack, copied into the scratch array
-    const int ni = D.order + 1, nq = D.nq1d;
-    double tab[2 * kTableMax];
-    host_basis_tables(ni, nq, tab, tab + nq * ni, tab + 2 * nq * ni);
-    const int tabn = 2 * nq * ni + nq;
-    df *tabw = reinterpret_cast<df *>(tab + kTableMax);
-    for (int i = 0; i < tabn; ++i) tabw[i] = df(tab[i]);
-    cudaError_t e = cudaMemcpyAsync(scratch + kTableOffset, tab, sizeof(double) * 2 * kTableMax,
-                                    cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("table copy: ") + cudaGetErrorString(e));
-
+    // the tables of this configuration, written by the first call on the device
+    const double *tab = scratch + kTableOffset + sl * kSlotDoubles;
     ElemParams P;
     P.map = elem_to_node;
     P.E = D.num_elems;
     P.Nx = D.num_nodes;
-    P.tab = scratch + kTableOffset;
+    P.tab = tab;
     P.tabf = nullptr;
-    P.tabw = reinterpret_cast<const df *>(scratch + kTableOffset + kTableMax);
+    P.tabw = reinterpret_cast<const df *>(tab + kTableMax);
     P.metric = D.metric;
     P.target = D.target;
     P.h0 = D.target_h0;
     // every partial slot the reduction reads is written by this launch, so
     // nothing in the scratch needs clearing first
     const int arith = D.hess_precision == TMOP_FP64_NATIVE ? ARITH_NATIVE : ARITH_DW;
-    e = launch_energy(D.dim, D.order, D.nq1d, P, x, scratch, arith, s);
+    cudaError_t e = launch_energy(D.dim, D.order, D.nq1d, P, x, scratch, arith, s);
     if (e == cudaSuccess) e = launch_finalize_energy(scratch, nb, out, s);
     if (e != cudaSuccess) return set_error(TMOP_ERR_CUDA, std::string("energy launch: ") + cudaGetErrorString(e));
     return TMOP_OK;

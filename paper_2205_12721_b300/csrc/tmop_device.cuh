@@ -65,7 +65,6 @@ struct ElemParams {
     int metric, target;
     double h0;
     const double *__restrict__ eta = nullptr;   // nodal field of the discrete target (Nx)
-    int energy_fp64 = 0;     // fused energy from FP64 invariants (near a zero-energy optimum)
     double *__restrict__ detq = nullptr;        // k_energy: det A at every point (E x NQD) when set
 };
 
