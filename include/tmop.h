@@ -395,6 +395,36 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int kernel_class, double *total_ms,
 /* Bytes of device memory the context holds. */
 int64_t tmop_device_bytes(const tmop_ctx *ctx);
 
+/* ---- Vector algebra for a caller-driven Krylov iteration ---------------
+ * The element-partitioned Newton step of several ranks (the P operator of
+ * Sec. 3 applied per rank, interface sums between ranks; see dist.py) runs
+ * its Jacobi-MINRES (Sec. 2.3) on the host, with these kernels for the
+ * vector work on each rank's local DOFs.  Device FP64 arrays of n values,
+ * enqueued on the context's stream; out may alias an input.
+ *   tmop_vec_lincomb  out = a x + b y + c z  (y or z NULL: term absent)
+ *   tmop_vec_mul      out = x .* y
+ *   tmop_vec_dot      *out (host) = sum_i x_i y_i over the entries with
+ *                     mask_i != 0 (mask: device uint8, or NULL for all);
+ *                     a fixed summation order; synchronises.
+ * Errors: TMOP_ERR_ARG for NULL inputs or n < 0. */
+tmop_status tmop_vec_lincomb(tmop_ctx *ctx, int64_t n, double a, const double *x, double b,
+                             const double *y, double c, const double *z, double *out);
+tmop_status tmop_vec_mul(tmop_ctx *ctx, int64_t n, const double *x, const double *y, double *out);
+tmop_status tmop_vec_dot(tmop_ctx *ctx, int64_t n, const double *x, const double *y,
+                         const uint8_t *mask, double *out);
+
+/* The Jacobi preconditioner of the Newton step's MINRES (Sec. 3.4):
+ * minv_i = 1/|diag_i|, 1 where |diag_i| < 1e-300. */
+tmop_status tmop_vec_jacobi(tmop_ctx *ctx, int64_t n, const double *diag, double *minv);
+
+/* Interface-sum packing: dst[k] = src[idx[k]] (gather) and
+ * dst[idx[k]] += vals[k] (scatter-add; the m indices must be distinct).
+ * idx: device int32, m entries in range (not checked). */
+tmop_status tmop_vec_gather(tmop_ctx *ctx, int64_t m, const int32_t *idx, const double *src,
+                            double *dst);
+tmop_status tmop_vec_scatter_add(tmop_ctx *ctx, int64_t m, const int32_t *idx, const double *vals,
+                                 double *dst);
+
 /* ---- Fault injection for the tests of the failure paths (host side) -----
  * No GPU fault is involved: the library pretends, on the host, that a
  * computation failed, and the tests check what the caller then sees. */

@@ -33,7 +33,9 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_batch_device_bytes", "tmop_batch_destroy", "tmop_set_limit_reference",
            "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det",
            "tmop_apply_variants", "tmop_get_apply_variant", "tmop_set_apply_variant",
-           "tmop_autotune", "tmop_inject_fault", "tmop_batch_inject_fault")
+           "tmop_autotune", "tmop_inject_fault", "tmop_batch_inject_fault",
+           "tmop_vec_lincomb", "tmop_vec_mul", "tmop_vec_dot", "tmop_vec_gather",
+           "tmop_vec_scatter_add", "tmop_vec_jacobi")
 
 
 class TmopError(RuntimeError):
@@ -120,6 +122,12 @@ def lib():
             "tmop_set_apply_variant": (I, [I, I, I, I, I]),
             "tmop_autotune": (I, [P, I, ctypes.POINTER(I), P]),
             "tmop_inject_fault": (I, [P, I]),
+            "tmop_vec_lincomb": (I, [P, I64, D, P, D, P, D, P, P]),
+            "tmop_vec_mul": (I, [P, I64, P, P, P]),
+            "tmop_vec_dot": (I, [P, I64, P, P, P, ctypes.POINTER(D)]),
+            "tmop_vec_gather": (I, [P, I64, P, P, P]),
+            "tmop_vec_jacobi": (I, [P, I64, P, P]),
+            "tmop_vec_scatter_add": (I, [P, I64, P, P, P]),
             "tmop_batch_inject_fault": (I, [P, I, I]),
             "tmop_hessian_setup": (I, [P, P]),
             "tmop_hessian_apply": (I, [P, P, P]),
@@ -228,6 +236,39 @@ def tmop_autotune(ctx: int, reps: int = 10):
     while times and times[-1] != times[-1]:      # drop the unused (NaN) slots
         times.pop()
     return v.value, times
+
+
+def tmop_vec_lincomb(ctx: int, out, a, x, b=0.0, y=None, c=0.0, z=None):
+    """out = a x + b y + c z on device FP64 tensors (y, z optional)."""
+    _check(lib().tmop_vec_lincomb(ctx, out.numel(), float(a), _ptr(x), float(b), _ptr(y), float(c),
+                                  _ptr(z), _ptr(out)), "tmop_vec_lincomb")
+
+
+def tmop_vec_mul(ctx: int, out, x, y):
+    _check(lib().tmop_vec_mul(ctx, out.numel(), _ptr(x), _ptr(y), _ptr(out)), "tmop_vec_mul")
+
+
+def tmop_vec_dot(ctx: int, x, y, mask=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check(lib().tmop_vec_dot(ctx, x.numel(), _ptr(x), _ptr(y), _ptr(mask), ctypes.byref(out)),
+           "tmop_vec_dot")
+    return out.value
+
+
+def tmop_vec_jacobi(ctx: int, diag, minv):
+    """minv = 1/|diag| (1 where |diag| < 1e-300)."""
+    _check(lib().tmop_vec_jacobi(ctx, diag.numel(), _ptr(diag), _ptr(minv)), "tmop_vec_jacobi")
+
+
+def tmop_vec_gather(ctx: int, idx, src, dst):
+    """dst[k] = src[idx[k]] (idx: device int32 tensor)."""
+    _check(lib().tmop_vec_gather(ctx, idx.numel(), _ptr(idx), _ptr(src), _ptr(dst)), "tmop_vec_gather")
+
+
+def tmop_vec_scatter_add(ctx: int, idx, vals, dst):
+    """dst[idx[k]] += vals[k] (distinct indices)."""
+    _check(lib().tmop_vec_scatter_add(ctx, idx.numel(), _ptr(idx), _ptr(vals), _ptr(dst)),
+           "tmop_vec_scatter_add")
 
 
 FAULT_NONE, FAULT_MINRES_BREAKDOWN = 0, 1

@@ -982,6 +982,57 @@ tmop_status tmop_profile_read(tmop_ctx *ctx, int cls, double *total_ms, int64_t 
 
 int64_t tmop_device_bytes(const tmop_ctx *ctx) { return ctx ? ctx->bytes : 0; }
 
+tmop_status tmop_vec_lincomb(tmop_ctx *ctx, int64_t n, double a, const double *x, double b,
+                             const double *y, double c, const double *z, double *out)
+{
+    if (!ctx || !x || !out || n < 0) return fail(TMOP_ERR_ARG, "NULL argument or n < 0");
+    CK(launch_lincomb(n, a, x, b, y, c, z, out, ctx->stream));
+    return TMOP_OK;
+}
+
+tmop_status tmop_vec_mul(tmop_ctx *ctx, int64_t n, const double *x, const double *y, double *out)
+{
+    if (!ctx || !x || !y || !out || n < 0) return fail(TMOP_ERR_ARG, "NULL argument or n < 0");
+    CK(launch_vmul(n, x, y, out, ctx->stream));
+    return TMOP_OK;
+}
+
+tmop_status tmop_vec_dot(tmop_ctx *ctx, int64_t n, const double *x, const double *y,
+                         const uint8_t *mask, double *out)
+{
+    if (!ctx || !x || !y || !out || n < 0) return fail(TMOP_ERR_ARG, "NULL argument or n < 0");
+    const int nb = reduce_blocks(n);
+    CK(launch_dot_masked(x, y, mask, n, ctx->part, nb, ctx->stream));
+    CK(launch_finalize_sum(ctx->part, nb, ctx->scal + 3, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hscal + 3, ctx->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = ctx->hscal[3];
+    return TMOP_OK;
+}
+
+tmop_status tmop_vec_jacobi(tmop_ctx *ctx, int64_t n, const double *diag, double *minv)
+{
+    if (!ctx || !diag || !minv || n < 0) return fail(TMOP_ERR_ARG, "NULL argument or n < 0");
+    CK(launch_jacobi(diag, TMOP_FP64, n, minv, ctx->stream));
+    return TMOP_OK;
+}
+
+tmop_status tmop_vec_gather(tmop_ctx *ctx, int64_t m, const int32_t *idx, const double *src,
+                            double *dst)
+{
+    if (!ctx || m < 0 || (m > 0 && (!idx || !src || !dst))) return fail(TMOP_ERR_ARG, "NULL argument or m < 0");
+    CK(launch_vgather(m, idx, src, dst, ctx->stream));
+    return TMOP_OK;
+}
+
+tmop_status tmop_vec_scatter_add(tmop_ctx *ctx, int64_t m, const int32_t *idx, const double *vals,
+                                 double *dst)
+{
+    if (!ctx || m < 0 || (m > 0 && (!idx || !vals || !dst))) return fail(TMOP_ERR_ARG, "NULL argument or m < 0");
+    CK(launch_vscatter_add(m, idx, vals, dst, ctx->stream));
+    return TMOP_OK;
+}
+
 tmop_status tmop_inject_fault(tmop_ctx *ctx, int fault)
 {
     if (!ctx || (fault != TMOP_FAULT_NONE && fault != TMOP_FAULT_MINRES_BREAKDOWN))

@@ -108,6 +108,15 @@ cudaError_t launch_trial(const double *x, const double *dx, double alpha, int64_
                          cudaStream_t s);
 cudaError_t launch_dot(const void *a, const void *b, int prec, int64_t n, double *part, int nb,
                        cudaStream_t s);
+cudaError_t launch_dot_masked(const double *a, const double *b, const uint8_t *mask, int64_t n,
+                              double *part, int nb, cudaStream_t s);
+cudaError_t launch_lincomb(int64_t n, double a, const double *x, double b, const double *y,
+                           double c, const double *z, double *out, cudaStream_t s);
+cudaError_t launch_vmul(int64_t n, const double *x, const double *y, double *out, cudaStream_t s);
+cudaError_t launch_vgather(int64_t m, const int32_t *idx, const double *src, double *dst,
+                           cudaStream_t s);
+cudaError_t launch_vscatter_add(int64_t m, const int32_t *idx, const double *vals, double *dst,
+                                cudaStream_t s);
 cudaError_t launch_finalize_sum(const double *part, int nb, double *out, cudaStream_t s);
 cudaError_t launch_finalize_energy(const double *part, int64_t nb, double *out, cudaStream_t s);
 cudaError_t launch_jacobi(const void *diag, int prec, int64_t n, void *minv, cudaStream_t s);

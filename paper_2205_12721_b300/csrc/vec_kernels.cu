@@ -303,7 +303,97 @@ inline unsigned grid_for(int64_t n)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Vector algebra for callers that drive their own Krylov iteration.
+__global__ void k_lincomb(int64_t n, double a, const double *__restrict__ x, double b,
+                          const double *__restrict__ y, double c, const double *__restrict__ z,
+                          double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = a * x[i];
+        if (y) v += b * y[i];
+        if (z) v += c * z[i];
+        out[i] = v;
+    }
+}
+
+__global__ void k_vmul(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] * y[i];
+}
+
+// partial sums of x_i y_i over the entries with mask_i != 0 (all when mask is null)
+__global__ void k_dot_masked(const double *__restrict__ a, const double *__restrict__ b,
+                             const uint8_t *__restrict__ mask, int64_t n, double *__restrict__ part)
+{
+    __shared__ double sh[VT / 32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!mask || mask[i]) s += a[i] * b[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_vgather(int64_t m, const int32_t *__restrict__ idx, const double *__restrict__ src,
+                          double *__restrict__ dst)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[idx[k]];
+}
+
+// dst[idx[k]] += vals[k]; the indices of one call are distinct (no atomics)
+__global__ void k_vscatter_add(int64_t m, const int32_t *__restrict__ idx,
+                               const double *__restrict__ vals, double *__restrict__ dst)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[k]] += vals[k];
+}
+
 }  // namespace
+
+cudaError_t launch_vgather(int64_t m, const int32_t *idx, const double *src, double *dst,
+                           cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    k_vgather<<<grid_for(m), VT, 0, s>>>(m, idx, src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vscatter_add(int64_t m, const int32_t *idx, const double *vals, double *dst,
+                                cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    k_vscatter_add<<<grid_for(m), VT, 0, s>>>(m, idx, vals, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(int64_t n, double a, const double *x, double b, const double *y,
+                           double c, const double *z, double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_lincomb<<<grid_for(n), VT, 0, s>>>(n, a, x, b, y, c, z, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vmul(int64_t n, const double *x, const double *y, double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_vmul<<<grid_for(n), VT, 0, s>>>(n, x, y, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_masked(const double *a, const double *b, const uint8_t *mask, int64_t n,
+                              double *part, int nb, cudaStream_t s)
+{
+    k_dot_masked<<<nb, VT, 0, s>>>(a, b, mask, n, part);
+    count_launch();
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- remap CG / RK4
 // Jacobi-preconditioned CG for the mass solves of the advection remap
