@@ -88,7 +88,9 @@ __device__ __forceinline__ double cvt_out(const df &v) { return (double)v; }
 __device__ __forceinline__ double cvt_out(double v) { return v; }
 __device__ __forceinline__ float cvt_out(float v) { return v; }
 
-template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB>
+// PFN (rolled shared-memory columns): prefetch the next point's stored values
+// into L2 while the current point is multiplied.
+template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB, bool PFN = false>
 __global__ void __launch_bounds__(Apply3cShape<C, WPB>::NT, MINB)
 k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
           const int *__restrict__ stop_iter, int k, BatchArgs BA, int64_t ntiles,
@@ -258,6 +260,11 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
 #pragma unroll(SC && ROLL ? 1 : NQ)
         for (int q3 = 0; q3 < NQ; ++q3) {
             const RC *Hq = He + q3 * NQ * NQ;
+            if (PFN && q3 + 1 < NQ) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(Hq + NQ * NQ + s * NQD));
+            }
             RC d[9], y[9];
 #pragma unroll
             for (int r = 0; r < 9; ++r) d[r] = COLW(r, q3);

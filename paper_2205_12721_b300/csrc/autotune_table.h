@@ -18,19 +18,19 @@ static const ApplyTuned kApplyTuned[] = {
     {3, 1, 3, 0, 3},
     {3, 1, 3, 1, 1},
     {3, 1, 3, 2, 0},
-    {3, 2, 3, 0, 3},
+    {3, 2, 3, 0, 8},
     {3, 2, 3, 1, 4},
     {3, 2, 3, 2, 1},
     {3, 2, 4, 0, 5},
-    {3, 2, 4, 1, 4},
+    {3, 2, 4, 1, 2},
     {3, 2, 4, 2, 1},
-    {3, 3, 4, 0, 5},
+    {3, 3, 4, 0, 7},
     {3, 3, 4, 1, 4},
     {3, 3, 4, 2, 6},
     {3, 3, 5, 0, 5},
     {3, 3, 5, 1, 5},
     {3, 3, 5, 2, 0},
-    {3, 4, 5, 0, 5},
+    {3, 4, 5, 0, 7},
     {3, 4, 5, 1, 5},
     {3, 4, 5, 2, 6},
 };

@@ -12,6 +12,8 @@
 //   5  as 3, 8 warps per CTA
 //   6  collocated, shared-memory column, point body unrolled, compiler's
 //      register budget, 4 warps per CTA
+//   7  as 5, with an L2 prefetch of the next point's stored values
+//   8  as 3, with the same prefetch
 #pragma once
 
 #include <type_traits>
@@ -38,7 +40,7 @@ static const ColTab<RC, NI, NQ> &coltab()
     return T;
 }
 
-template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true>
+template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true, bool PFN = false>
 static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                                int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
@@ -51,7 +53,7 @@ static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV
                                : (P.E + S::EPB - 1) / S::EPB;
     if (nb == 0) return cudaSuccess;
     const size_t bytes = S::template bytes<RC>(SC);
-    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB>;
+    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN>;
     cudaError_t e = prepare(kern, bytes);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nb, S::NT, bytes, s>>>(P, v, H, ev, stop, k, B, ntiles, coltab<RC, C::NI, C::NQ>());
@@ -99,7 +101,7 @@ static cudaError_t run_apply_legacy(const ElemParams &P, const RV *v, const RC *
 template <class C>
 constexpr int apply_variant_count()
 {
-    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 7 : 1;
+    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 9 : 1;
 }
 
 template <class C, class RV, class RC>
@@ -114,6 +116,8 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
             case 4: return run_apply3c<C, RV, RC, 2, true>(P, v, H, ev, stop, k, s, B, ntiles);
             case 5: return run_apply3c<C, RV, RC, 8, true>(P, v, H, ev, stop, k, s, B, ntiles);
             case 6: return run_apply3c<C, RV, RC, 4, true, false>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 7: return run_apply3c<C, RV, RC, 8, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 8: return run_apply3c<C, RV, RC, 4, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
             default: break;
         }
     }
