@@ -714,6 +714,50 @@ def run_serving(args):
             "by_rate": res}
 
 
+def run_split(args, rank, world, local_rank):
+    """The element-partitioned Newton step (dist.py) of the benchmark mesh over
+    the ranks (strong scaling: the mesh is fixed, each rank owns a slab of
+    elements, one interface sum per gradient / action / diagonal and
+    allreduced scalars over NCCL).  With one rank it measures the
+    host-driven distributed MINRES against the device MINRES of the default
+    bench line."""
+    import torch
+    from paper_2205_12721_b300 import capi, dist
+    torch.cuda.set_device(local_rank)
+    m = workload(args)
+    comm = dist.TorchComm() if world > 1 else dist.ThreadComm.group(1)[0]
+    part = dist.partition(m.map, m.num_nodes, 3, m.fixed, world, rank)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        be = dist.LibraryBackend(part, m.order, capi.METRIC_303, stream=s)
+        dn = dist.DistNewton(be, comm)
+        x0 = be.from_host(part.to_local(m.x, m.num_nodes))
+        x = x0.clone()
+        for _ in range(args.warmup):
+            x.copy_(x0)
+            dn.newton_step(x, 0.0, MINRES_ITS, True)
+        s.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            x.copy_(x0)
+            r = dn.newton_step(x, 0.0, MINRES_ITS, True)
+        s.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+    be.close()
+    dt = max_over_ranks(dt, world, torch.device("cuda", local_rank))
+    return {"metric": METRIC, "value": m.ndof * MINRES_ITS / dt / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64 (double-float contractions)",
+            "data": "synthetic seeded perturbed Cartesian mesh (no dataset)",
+            "config": {"workload": f"3D hex {m.n[0]}^3 Q{m.order}, mu_303, 1 element-partitioned Newton "
+                                   f"step with {MINRES_ITS} MINRES", "dofs": m.ndof,
+                       "parallelism": f"element partition x{world} (slabs), interface sums + allreduce"},
+            "newton": {"status": r["status"], "alpha": r["alpha"], "minres_iters": r["minres_iters"]}}
+
+
 def run_autotune(args):
     """The autotuner over the Hessian-action kernel variants: for every
     configuration with more than one variant (3D, p = 1..4, n_q = p+1 and p+2
@@ -769,7 +813,7 @@ def main():
                     help="other precisions timed after the main run (rank 0)")
     ap.add_argument("--workload", default="newton",
                     choices=["newton", "batched", "serving", "sweep", "solve", "kershaw", "remap",
-                             "autotune"])
+                             "autotune", "split"])
     ap.add_argument("--kershaw-orders", dest="kershaw_orders", type=int, nargs="+", default=[1, 2, 3, 4])
     ap.add_argument("--kershaw-precisions", dest="kershaw_precisions", nargs="+",
                     default=["fp64", "fp32"])
@@ -799,6 +843,18 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.workload == "split":
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_split(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.workload != "newton":
         out = {"batched": run_batched, "serving": run_serving, "sweep": run_sweep,
                "solve": run_solve, "kershaw": run_kershaw, "remap": run_remap,
