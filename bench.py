@@ -302,6 +302,7 @@ def run_ours(args, rank, world, local_rank):
                                      "kernel_ms": v["kernel_ms"]}
     if rank == 0 and not args.no_ttc and not args.no_cpu_baseline:
         out["time_to_converged"] = time_to_converged(args)
+        out["serving_sample"] = serving_sample(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     return out
@@ -356,6 +357,26 @@ def cpu_baseline(args, seconds=None):
                       f"same family ({ndof} DOFs), {cores} independent processes, {wall:.2f} s "
                       f"wall; single thread {dt1:.2f} s",
             "status": max([st] + [r[2] for r in res])}
+
+
+def serving_sample(args, n_jobs=100, rate=50.0):
+    """A bounded sample of the serving configuration: the first ``n_jobs``
+    requests of the Poisson stream (2D n_e U{8..128} mu_2 / 3D n_e U{4..40}
+    mu_302, p U{1..4}, gradient-norm rtol 1e-6) at ``rate`` requests/s,
+    continuous batching under a 64 GB budget; p50/p99 from arrival to
+    converged mesh and meshes/s."""
+    import torch
+    from paper_2205_12721_b300 import meshgen
+    from paper_2205_12721_b300.serve import Server, summarize
+    jobs = meshgen.serving_workload(n_jobs, rate=rate, n2=tuple(args.n2), n3=tuple(args.n3))
+    srv = Server(int(args.budget_gb * (1 << 30)), precision="fp64", newton_rtol=1e-6,
+                 newton_max_it=50, minres_max_it=50)
+    done = srv.run(jobs)
+    srv.close()
+    torch.cuda.synchronize()
+    s = summarize(done)
+    s.update({"requests": n_jobs, "rate_per_s": rate, "precision": "fp64-class"})
+    return s
 
 
 def time_to_converged(args, reps=5):
