@@ -107,3 +107,28 @@ def test_mixed_precision_final_energy(p):
         assert a["status"] == 0 and c["status"] == 0
         assert a["energy"] < a["energy0"]
         assert abs(a["energy"] - c["energy"]) <= 1e-8 * max(abs(a["energy"]), 1e-8 * m.num_elems), (a, c)
+
+
+def test_batch_rtol_stopped_minres_matches_oracle():
+    """The batched per-mesh MINRES stop test (phibar <= rtol beta1, Sec. 2.3)
+    against the oracle's: meshes perturbed mildly enough that MINRES converges
+    to rtol 1e-8 well before its cap (no tie in the stop test), the same
+    iteration count per step and iterates to 1e-10 h."""
+    d, p, metric = 3, 2, 302
+    meshes = [_mesh(d, p, s, 80 + i, amp=0.02) for i, s in enumerate([(3, 3, 2), (4, 3, 2), (2, 3, 3)])]
+    b = TmopBatch(d, p, metric, max_meshes=4, minres_rtol=1e-8, minres_max_it=200)
+    slots = [b.add_structured(m) for m in meshes]
+    for step in range(2):
+        xs = {s: _x(b, s) for s in slots}
+        its0 = {s: b.state(s)["minres_its"] for s in slots}
+        b.step()
+        for s, m in zip(slots, meshes):
+            om = O.Mesh(d, p, p + 1, m.map, m.num_nodes, metric, m.fixed)
+            xo = xs[s].copy()
+            ro = O.newton_step(om, xo, 1e-8, 200)
+            st = b.state(s)
+            assert ro["status"] == 0 and st["status"] == 0
+            assert ro["minres_iters"] < 200
+            assert st["minres_its"] - its0[s] == ro["minres_iters"], (step, s)
+            assert np.abs(_x(b, s) - xo).max() <= 1e-10 * m.h, (step, s)
+    b.close()
