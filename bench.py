@@ -52,7 +52,9 @@ APPLY_VARIANT_NAME = {0: "sum-factorised register column", 1: "collocated, regis
                       5: "collocated, shared-memory column, 8 warps/CTA",
                       6: "collocated, shared-memory column unrolled, 4 warps/CTA",
                       7: "collocated, shared-memory column, 8 warps/CTA, L2 prefetch of the next point",
-                      8: "collocated, shared-memory column, 4 warps/CTA, L2 prefetch of the next point"}
+                      8: "collocated, shared-memory column, 4 warps/CTA, L2 prefetch of the next point",
+                      9: "collocated, shared-memory column, 8 warps/CTA, L2 prefetch, chunked register pipeline",
+                      10: "collocated, shared-memory column, 4 warps/CTA, chunked register pipeline"}
 
 
 def flops_apply_per_elem(d, ni, nq, ns, collocated=False):

@@ -88,9 +88,38 @@ __device__ __forceinline__ double cvt_out(const df &v) { return (double)v; }
 __device__ __forceinline__ double cvt_out(double v) { return v; }
 __device__ __forceinline__ float cvt_out(float v) { return v; }
 
+// f(integral_constant<int, 0>), ..., f(integral_constant<int, N-1>), in order
+// (a loop whose index is a constant expression in the body).
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (N > 0) {
+        static_for<N - 1>(f);
+        f(std::integral_constant<int, N - 1>{});
+    }
+}
+
+// Row and column of the k-th entry of the packed upper triangle of a 9 x 9
+// symmetric matrix (the inverse of pidx<9>).
+__host__ __device__ constexpr int prow9(int k)
+{
+    int r = 0;
+    while (k >= 9 - r) {
+        k -= 9 - r;
+        ++r;
+    }
+    return r;
+}
+__host__ __device__ constexpr int pcol9(int k) { return prow9(k) + (k - pidx<9>(prow9(k), prow9(k))); }
+
 // PFN (rolled shared-memory columns): prefetch the next point's stored values
-// into L2 while the current point is multiplied.
-template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB, bool PFN = false>
+// into L2 while the current point is multiplied.  PIPE (shared-memory
+// columns): the thread's stored values, in order (point, packed entry), are
+// taken in chunks of 9 held in two register buffers, the loads of chunk j+1
+// issued before the multiply-adds of chunk j; the same arithmetic in the same
+// order as the plain point loop.
+template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB, bool PFN = false,
+          bool PIPE = false>
 __global__ void __launch_bounds__(Apply3cShape<C, WPB>::NT, MINB)
 k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
           const int *__restrict__ stop_iter, int k, BatchArgs BA, int64_t ntiles,
@@ -254,7 +283,59 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     }
 
     // ---- pointwise: Y = H : dA with the symmetric-packed stored data
-    if (valid) {
+    if (PIPE && SC && valid) {
+        static_assert(NS == 45, "3D packed data");
+        constexpr int CH = 9, NCH = 5;                  // 45 = 5 chunks of 9 per point
+        constexpr int NJ = NQ * NCH;
+        constexpr int UJ = (NQ % 2 == 0) ? 2 * NCH : NJ;   // chunks per unrolled body
+        const RC *He = H + e * (int64_t)(NS * NQD) + (ty * NQ + tx);
+        RC hb0[CH], hb1[CH];                            // the two chunk buffers
+#pragma unroll
+        for (int t2 = 0; t2 < CH; ++t2) hb0[t2] = ld_stream(He + t2 * NQD);
+#pragma unroll 1
+        for (int j0 = 0; j0 < NJ; j0 += UJ) {
+            RC d[9], y[9];
+            static_for<UJ>([&](auto JJ) {
+                constexpr int jj = decltype(JJ)::value;
+                constexpr int c = jj % NCH;             // chunk of the point
+                constexpr int c1 = (jj + 1) % NCH;
+                RC *cur = (jj & 1) ? hb1 : hb0;
+                RC *nxt = (jj & 1) ? hb0 : hb1;
+                const int q3 = j0 / NCH + jj / NCH;
+                if (j0 + jj + 1 < NJ) {                 // loads of the next chunk
+                    const RC *Hn = He + (j0 / NCH + (jj + 1) / NCH) * NQ * NQ + c1 * CH * NQD;
+#pragma unroll
+                    for (int t2 = 0; t2 < CH; ++t2) nxt[t2] = ld_stream(Hn + t2 * NQD);
+                    if (PFN && c == 0 && q3 + 1 < NQ) {
+#pragma unroll
+                        for (int s2 = 0; s2 < NS; ++s2)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(He + (q3 + 1) * NQ * NQ + s2 * NQD));
+                    }
+                }
+                if constexpr (c == 0) {
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) d[r] = COLW(r, q3);
+                }
+                static_for<CH>([&](auto T2) {
+                    constexpr int t2 = decltype(T2)::value;
+                    constexpr int kk = c * CH + t2;     // packed entry
+                    constexpr int r = prow9(kk), sc = pcol9(kk);
+                    const RC h = cur[t2];
+                    if constexpr (r == 0) {             // row 0 starts every sum
+                        y[sc] = mul1(h, d[0]);
+                        if constexpr (sc > 0) acc_add(y[0], h * d[sc]);
+                    } else {
+                        acc_add(y[sc], h * d[r]);
+                        if constexpr (sc != r) acc_add(y[r], h * d[sc]);
+                    }
+                });
+                if constexpr (c == NCH - 1) {
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) COLW(r, q3) = y[r];
+                }
+            });
+        }
+    } else if (valid) {
         const RC *He = H + e * (int64_t)(NS * NQD) + (ty * NQ + tx);
         // ROLL (shared-memory columns only): one copy of the point body
 #pragma unroll(SC && ROLL ? 1 : NQ)

@@ -14,6 +14,8 @@
 //      register budget, 4 warps per CTA
 //   7  as 5, with an L2 prefetch of the next point's stored values
 //   8  as 3, with the same prefetch
+//   9  as 7, the stored values taken in register-double-buffered chunks of 9
+//  10  as 3, the same chunked stream (no L2 prefetch)
 #pragma once
 
 #include <type_traits>
@@ -40,7 +42,8 @@ static const ColTab<RC, NI, NQ> &coltab()
     return T;
 }
 
-template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true, bool PFN = false>
+template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true, bool PFN = false,
+          bool PIPE = false>
 static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                                int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
@@ -53,7 +56,7 @@ static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV
                                : (P.E + S::EPB - 1) / S::EPB;
     if (nb == 0) return cudaSuccess;
     const size_t bytes = S::template bytes<RC>(SC);
-    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN>;
+    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN, PIPE>;
     cudaError_t e = prepare(kern, bytes);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nb, S::NT, bytes, s>>>(P, v, H, ev, stop, k, B, ntiles, coltab<RC, C::NI, C::NQ>());
@@ -101,7 +104,7 @@ static cudaError_t run_apply_legacy(const ElemParams &P, const RV *v, const RC *
 template <class C>
 constexpr int apply_variant_count()
 {
-    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 9 : 1;
+    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 11 : 1;
 }
 
 template <class C, class RV, class RC>
@@ -118,6 +121,8 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
             case 6: return run_apply3c<C, RV, RC, 4, true, false>(P, v, H, ev, stop, k, s, B, ntiles);
             case 7: return run_apply3c<C, RV, RC, 8, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
             case 8: return run_apply3c<C, RV, RC, 4, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 9: return run_apply3c<C, RV, RC, 8, true, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 10: return run_apply3c<C, RV, RC, 4, true, true, false, true>(P, v, H, ev, stop, k, s, B, ntiles);
             default: break;
         }
     }
