@@ -40,7 +40,7 @@ MINRES_ITS = 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one action launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {"fp64": 2.699e9, "fp32": 1.375e9}     # variants 7 (fp64 class) and 4 (fp32)
+TRAFFIC_BYTES = {("fp64", 7): 2.699e9, ("fp32", 4): 1.375e9}     # (precision, action variant)
 PRECISION_LABEL = {"fp64": "fp64-class (double-float contractions, 48-bit significand)",
                    "fp32": "fp32-mixed (fp32 stored d2mu/dT2, action and MINRES; fp64 residual, "
                            "energy, det and line search)",
@@ -54,7 +54,13 @@ APPLY_VARIANT_NAME = {0: "sum-factorised register column", 1: "collocated, regis
                       7: "collocated, shared-memory column, 8 warps/CTA, L2 prefetch of the next point",
                       8: "collocated, shared-memory column, 4 warps/CTA, L2 prefetch of the next point",
                       9: "collocated, shared-memory column, 8 warps/CTA, L2 prefetch, chunked register pipeline",
-                      10: "collocated, shared-memory column, 4 warps/CTA, chunked register pipeline"}
+                      10: "collocated, shared-memory column, 4 warps/CTA, chunked register pipeline",
+                      11: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 20 (FP32 32) warps/SM",
+                      12: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 24 warps/SM",
+                      13: "collocated, per-warp shared-memory column with aliased buffers, 8 warps/CTA, 24 warps/SM, L2 prefetch",
+                      14: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 20 (FP32 32) warps/SM, L2 prefetch",
+                      15: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 24 warps/SM, L2 prefetch",
+                      16: "collocated, per-warp shared-memory column with aliased buffers, 8 warps/CTA, 24 warps/SM"}
 
 
 def flops_apply_per_elem(d, ni, nq, ns, collocated=False):
@@ -243,6 +249,9 @@ def run_ours(args, rank, world, local_rank):
     var = capi.tmop_get_apply_variant(d, p, nq, {"fp64": capi.FP64, "fp32": capi.FP32,
                                                  "fp64-native": capi.FP64_NATIVE}[args.precision])
     flops = flops_apply_per_elem(d, ni, nq, ns, collocated=var > 0) * E
+    traffic = args.traffic
+    if traffic is None and args.n_e == 48 and p == 3 and nq == 4:
+        traffic = TRAFFIC_BYTES.get((args.precision, var))
     rc_name = {"fp64": "double,df", "fp32": "float,float", "fp64-native": "double,double"}[args.precision]
     kname = (f"k_apply3c<Cfg<{d},{p},{nq}>,{rc_name},...> variant {var} ({APPLY_VARIANT_NAME[var]})"
              if var > 0 else f"k_apply3<Cfg<{d},{p},{nq}>,{rc_name}> variant 0")
@@ -252,14 +261,14 @@ def run_ours(args, rank, world, local_rank):
     if args.precision == "fp64-native":
         ach = flops / (apply_avg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "nominal FP64 rate of the profiling recipe",
                 "kernel": kname, "flops_per_launch": flops,
                 "hbm_view": {"achieved_gbs": gbs, "peak_gbs": hbm,
                              "frac": (gbs / hbm) if hbm else None, "bytes_per_launch": byts}}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                "frac": (gbs / hbm) if hbm else None, "traffic": args.traffic,
+                "frac": (gbs / hbm) if hbm else None, "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "kernel": kname,
                 "bytes_per_launch": byts,
@@ -297,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
                 continue
             sub = argparse.Namespace(**vars(args))
             sub.precision, sub.variants, sub.no_cpu_baseline = prec, [], True
-            sub.traffic = TRAFFIC_BYTES.get(prec) if (args.n_e == 48 and args.order == 3) else None
+            sub.traffic = None
             v = run_ours(sub, 0, 1, local_rank)
             out["variants"][prec] = {"value": v["value"], "ms_per_step": v["ms_per_step"],
                                      "dtype": v["dtype"], "roofline": v["roofline"],
@@ -861,8 +870,6 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="override the ncu dram bytes per launch of the apply kernel")
     args = ap.parse_args()
-    if args.traffic is None and args.n_e == 48 and args.order == 3:
-        args.traffic = TRAFFIC_BYTES.get(args.precision)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -230,7 +230,7 @@ def tmop_set_apply_variant(dim: int, order: int, nq1d: int, precision: int, vari
 def tmop_autotune(ctx: int, reps: int = 10):
     """(chosen variant, [ms per launch of variant 0, 1, ...])."""
     v = ctypes.c_int(0)
-    ms = (ctypes.c_double * 16)(*([float("nan")] * 16))
+    ms = (ctypes.c_double * 32)(*([float("nan")] * 32))
     _check(lib().tmop_autotune(ctx, reps, ctypes.byref(v), ms), "tmop_autotune")
     times = [float(t) for t in ms]
     while times and times[-1] != times[-1]:      # drop the unused (NaN) slots

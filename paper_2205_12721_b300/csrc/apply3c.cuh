@@ -27,7 +27,13 @@
 //               warps); ROLL keeps one copy of the point body (less code);
 //   WPB         warps per CTA (2, 4 or 8); a warp finds its own element tile,
 //               so a CTA may span two tiles of a batched launch;
-//   MINB        minimum resident CTAs per SM asked of the register allocator.
+//   MINB        minimum resident CTAs per SM asked of the register allocator;
+//   AL          (shared-memory columns) the columns are blocked per warp and
+//               the two contraction buffers live in column rows that are dead
+//               at the time: rows 6-8 (component 2) during the forward pass,
+//               rows 0-2 (component 0) during the transposed pass, which
+//               frees 2 x BUF values per element of shared memory for more
+//               resident CTAs.
 #pragma once
 
 #include <type_traits>
@@ -55,10 +61,13 @@ struct Apply3cShape {
     static constexpr int BUF = C::NQ * C::NQ * C::NQ;          // >= NP, NQ NI^2, NQ^2 NI
     static constexpr int NPL = (C::NP + TPE - 1) / TPE;        // map entries per lane
     static constexpr int TABN = C::NQ * C::NI + C::NQ * C::NQ;
+    // the two buffers of a warp's elements fit in three column rows of the warp
+    static_assert(2 * EPW * BUF <= 3 * C::NQ * 32, "aliased buffers");
     template <class R>
-    static constexpr size_t bytes(bool sc)
+    static constexpr size_t bytes(bool sc, bool al = false)
     {
-        return sizeof(R) * (size_t)(((TABN + 1) & ~1) + EPB * 2 * BUF + (sc ? 9 * C::NQ * NT : 0));
+        return sizeof(R) * (size_t)(((TABN + 1) & ~1) + (al ? 0 : EPB * 2 * BUF) +
+                                    (sc ? 9 * C::NQ * NT : 0));
     }
 };
 
@@ -119,7 +128,7 @@ __host__ __device__ constexpr int pcol9(int k) { return prow9(k) + (k - pidx<9>(
 // issued before the multiply-adds of chunk j; the same arithmetic in the same
 // order as the plain point loop.
 template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB, bool PFN = false,
-          bool PIPE = false>
+          bool PIPE = false, bool AL = false>
 __global__ void __launch_bounds__(Apply3cShape<C, WPB>::NT, MINB)
 k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
           const int *__restrict__ stop_iter, int k, BatchArgs BA, int64_t ntiles,
@@ -167,10 +176,17 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     }
     if (stop && *stop < k) return;                          // MINRES already stopped
 
-    RC *b0 = Bs + ((S::TABN + 1) & ~1) + el * 2 * BUF;
+    static_assert(!AL || SC, "aliased buffers need shared-memory columns");
+    // SC: the dA / Y columns of every thread, [(r * NQ + q3) * NT + thread],
+    // or with AL blocked per warp, [warp][(r * NQ + q3) * 32 + lane]
+    constexpr int CST = AL ? 32 : S::NT;                    // stride of a column row
+    RC *cs = Bs + ((S::TABN + 1) & ~1) + (AL ? warp * 9 * NQ * 32 : S::EPB * 2 * BUF);
+    const int ci = AL ? lane : threadIdx.x;                 // the thread's column
+    // AL: the buffers of the forward pass in rows 6-8 (component 2), of the
+    // transposed pass in rows 0-2 (component 0)
+    RC *b0 = AL ? cs + 6 * NQ * 32 + (act ? slot : 0) * 2 * BUF
+                : Bs + ((S::TABN + 1) & ~1) + el * 2 * BUF;
     RC *b1 = b0 + BUF;
-    // SC: the dA / Y columns of every thread, [(r * NQ + q3) * NT + thread]
-    RC *cs = Bs + ((S::TABN + 1) & ~1) + S::EPB * 2 * BUF;
     const int64_t e = e0 + (act ? slot : 0);
     const bool valid = act && e < P.E;
     int m[S::NPL];
@@ -181,7 +197,7 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     }
 
     RC col[SC ? 1 : 9][NQ];                                 // dA_{cb} then Y_{cb} at (tx, ty, q3)
-#define COLW(r, q3) (SC ? cs[((r) * NQ + (q3)) * S::NT + threadIdx.x] : col[SC ? 0 : (r)][q3])
+#define COLW(r, q3) (SC ? cs[((r) * NQ + (q3)) * CST + ci] : col[SC ? 0 : (r)][q3])
 
     // ---- forward: values at the points, then the collocated derivative
 #pragma unroll 1
@@ -258,12 +274,15 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                 g0[q3] = a;
                 g1[q3] = b;
             }
+        }
+        if (AL && c == 2) __syncwarp();                     // rows 6-8 held the buffers
+        if (valid) {
             if (SC) {
 #pragma unroll
                 for (int q3 = 0; q3 < NQ; ++q3) {
-                    cs[((c * 3 + 0) * NQ + q3) * S::NT + threadIdx.x] = g0[q3];
-                    cs[((c * 3 + 1) * NQ + q3) * S::NT + threadIdx.x] = g1[q3];
-                    cs[((c * 3 + 2) * NQ + q3) * S::NT + threadIdx.x] = g2[q3];
+                    cs[((c * 3 + 0) * NQ + q3) * CST + ci] = g0[q3];
+                    cs[((c * 3 + 1) * NQ + q3) * CST + ci] = g1[q3];
+                    cs[((c * 3 + 2) * NQ + q3) * CST + ci] = g2[q3];
                 }
             } else {
                 // c is a loop variable: select the register rows with unrolled tests
@@ -369,16 +388,21 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     }
 
     // ---- transposed: D^T along each direction, then B^T along q3, q2, q1
+    if (AL) {
+        b0 = cs + (act ? slot : 0) * 2 * BUF;
+        b1 = b0 + BUF;
+    }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         RC Y0[NQ], Y1[NQ], Y2[NQ];
         if (SC) {
 #pragma unroll
             for (int q3 = 0; q3 < NQ; ++q3) {
-                Y0[q3] = cs[((c * 3 + 0) * NQ + q3) * S::NT + threadIdx.x];
-                Y1[q3] = cs[((c * 3 + 1) * NQ + q3) * S::NT + threadIdx.x];
-                Y2[q3] = cs[((c * 3 + 2) * NQ + q3) * S::NT + threadIdx.x];
+                Y0[q3] = cs[((c * 3 + 0) * NQ + q3) * CST + ci];
+                Y1[q3] = cs[((c * 3 + 1) * NQ + q3) * CST + ci];
+                Y2[q3] = cs[((c * 3 + 2) * NQ + q3) * CST + ci];
             }
+            if (AL && c == 0) __syncwarp();                 // rows 0-2 become the buffers
         } else {
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc)

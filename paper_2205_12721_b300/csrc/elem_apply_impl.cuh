@@ -16,6 +16,13 @@
 //   8  as 3, with the same prefetch
 //   9  as 7, the stored values taken in register-double-buffered chunks of 9
 //  10  as 3, the same chunked stream (no L2 prefetch)
+//  11  as 3 with the buffers aliased into dead column rows, a register budget
+//      for 20 (FP32: 32) resident warps per SM
+//  12  as 11, a register budget for 24 resident warps
+//  13  as 12 with 8 warps per CTA and the L2 prefetch
+//  14  as 11 with the L2 prefetch
+//  15  as 12 with the L2 prefetch
+//  16  as 13 without the L2 prefetch
 #pragma once
 
 #include <type_traits>
@@ -42,21 +49,22 @@ static const ColTab<RC, NI, NQ> &coltab()
     return T;
 }
 
+// RW: resident warps per SM asked of the register allocator (0: 16 for
+// double-float / FP64, 24 for FP32, with rolled shared-memory columns; none
+// otherwise).
 template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true, bool PFN = false,
-          bool PIPE = false>
+          bool PIPE = false, bool AL = false, int RW = 0>
 static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                                int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
     using S = Apply3cShape<C, WPB>;
-    // rolled shared-memory columns: ask for the register budget of 512
-    // (double-float, FP64) or 768 (FP32) resident threads per SM; otherwise none
     constexpr bool F32 = std::is_same<RC, float>::value;
-    constexpr int MINB = (SC && ROLL) ? (F32 ? 24 : 16) / WPB : 0;
+    constexpr int MINB = RW > 0 ? RW / WPB : (SC && ROLL) ? (F32 ? 24 : 16) / WPB : 0;
     const int64_t nb = B.tiles ? (ntiles * C::EPB + S::EPB - 1) / S::EPB
                                : (P.E + S::EPB - 1) / S::EPB;
     if (nb == 0) return cudaSuccess;
-    const size_t bytes = S::template bytes<RC>(SC);
-    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN, PIPE>;
+    const size_t bytes = S::template bytes<RC>(SC, AL);
+    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN, PIPE, AL>;
     cudaError_t e = prepare(kern, bytes);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nb, S::NT, bytes, s>>>(P, v, H, ev, stop, k, B, ntiles, coltab<RC, C::NI, C::NQ>());
@@ -104,7 +112,7 @@ static cudaError_t run_apply_legacy(const ElemParams &P, const RV *v, const RC *
 template <class C>
 constexpr int apply_variant_count()
 {
-    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 11 : 1;
+    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 17 : 1;
 }
 
 template <class C, class RV, class RC>
@@ -112,6 +120,7 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
                              int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles, int variant)
 {
     if constexpr (apply_variant_count<C>() > 1) {
+        constexpr bool F32 = std::is_same<RC, float>::value;
         switch (variant) {
             case 1: return run_apply3c<C, RV, RC, 4, false>(P, v, H, ev, stop, k, s, B, ntiles);
             case 2: return run_apply3c<C, RV, RC, 2, false>(P, v, H, ev, stop, k, s, B, ntiles);
@@ -123,6 +132,12 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
             case 8: return run_apply3c<C, RV, RC, 4, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
             case 9: return run_apply3c<C, RV, RC, 8, true, true, true, true>(P, v, H, ev, stop, k, s, B, ntiles);
             case 10: return run_apply3c<C, RV, RC, 4, true, true, false, true>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 11: return run_apply3c<C, RV, RC, 4, true, true, false, false, true, F32 ? 32 : 20>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 12: return run_apply3c<C, RV, RC, 4, true, true, false, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 13: return run_apply3c<C, RV, RC, 8, true, true, true, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 14: return run_apply3c<C, RV, RC, 4, true, true, true, false, true, F32 ? 32 : 20>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 15: return run_apply3c<C, RV, RC, 4, true, true, true, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 16: return run_apply3c<C, RV, RC, 8, true, true, false, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
             default: break;
         }
     }
