@@ -214,7 +214,7 @@ __device__ __forceinline__ void apply3_body(ElemParams P, const RV *__restrict__
                     acc_add(o, G[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1]);
                     acc_add(o, B[q1 * NI + tx] * s1[O1 + (i3 * NI + ty) * NQ + q1]);
                 }
-                out[(i3 * NI + ty) * NI + tx] = RV(to_d(norm(o)));
+                ev_store(&out[(i3 * NI + ty) * NI + tx], norm(o));
             }
         }
     }
@@ -437,7 +437,7 @@ k_apply3s(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                     acc_add(o, G[q1 * NI + tx] * s1[(i3 * NI + ty) * NQ + q1]);
                     acc_add(o, B[q1 * NI + tx] * s1[O1 + (i3 * NI + ty) * NQ + q1]);
                 }
-                o_e[(i3 * NI + ty) * NI + tx] = RV(to_d(norm(o)));
+                ev_store(&o_e[(i3 * NI + ty) * NI + tx], norm(o));
             }
         }
         __syncthreads();      // s1 is reused by the next component

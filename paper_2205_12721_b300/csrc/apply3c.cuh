@@ -484,7 +484,7 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                 RC a = mul1(BTx[0], w[0]);
 #pragma unroll
                 for (int q1 = 1; q1 < NQ; ++q1) acc_add(a, BTx[q1] * w[q1]);
-                o_e[(i3 * NI + ty) * NI + tx] = RV(cvt_out(a));
+                ev_store(&o_e[(i3 * NI + ty) * NI + tx], a);
             }
         }
         __syncwarp();                                       // b0, b1 are reused by the next component

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "minres_scalar.cuh"
@@ -138,7 +139,7 @@ __global__ void b_assemble(const BMesh *M, const int2 *tiles, int ev_role, int o
         const int64_t t = bm.csr_idx[j];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a < D) asm_add(s[a], ev[a * ENP + t]);
+            if (a < D) asm_add(s[a], ld_plain(ev + a * ENP + t));
         if (((j - b) & 7) == 7)
 #pragma unroll
             for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
@@ -641,8 +642,18 @@ tmop_status setup_and_minres(tmop_batch *b)
         a = bargs(b, ROLE_KV0 + v, ROLE_H, ROLE_EVR, true);
         BCK(launch_apply(b->d, b->p, b->nq, P0, nullptr, nullptr, nullptr, b->desc.hess_precision,
                          nullptr, k, b->stream, &a, b->nt_e));
-        b_assemble<R, R><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z, 1,
-                                                          b->d, b->np, b->dS, k);
+        if constexpr (std::is_same<R, double>::value) {
+            if (D.hess_precision == TMOP_FP64)      // float-pair element vectors
+                b_assemble<df, double><<<b->nt_n, NCH, 0, b->stream>>>(
+                    b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z, 1, b->d, b->np, b->dS, k);
+            else
+                b_assemble<R, R><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EVR,
+                                                                  ROLE_KV0 + Z, 1, b->d, b->np,
+                                                                  b->dS, k);
+        } else {
+            b_assemble<R, R><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z,
+                                                              1, b->d, b->np, b->dS, k);
+        }
         b_lanczos_a<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R1, v, k);
         b_fin_alpha<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, k);
         b_lanczos_b<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R2, R1, k);

@@ -533,9 +533,9 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
             }));
         } else {
             TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
-                return launch_assemble(c->evR, c->vprec, c->csr_ptr, c->csr_idx, c->fixed, nullptr, 1,
-                                       c->Nx, c->d, c->ENP, Z, c->vprec, &c->st->stop_iter, k,
-                                       c->stream);
+                return launch_assemble(c->evR, action_ev_format(c->prec), c->csr_ptr, c->csr_idx,
+                                       c->fixed, nullptr, 1, c->Nx, c->d, c->ENP, Z, c->vprec,
+                                       &c->st->stop_iter, k, c->stream);
             }));
             CK(launch_lanczos_a(Z, R1, v, c->st, pr, n, k, c->part, nb, c->stream));
         }
@@ -803,8 +803,9 @@ tmop_status tmop_hessian_apply(tmop_ctx *ctx, const void *v, void *y)
         CK(launch_limit_apply(ctx->d, ctx->p, ctx->nq, P, ctx->vm, ctx->lim_cq, ctx->evR, ctx->prec,
                               nullptr, 0, ctx->stream));
     TRY(timed(ctx, TMOP_K_ASSEMBLE, "assemble", [&] {
-        return launch_assemble(ctx->evR, ctx->vprec, ctx->csr_ptr, ctx->csr_idx, ctx->fixed, v, 1,
-                               ctx->Nx, ctx->d, ctx->ENP, y, ctx->vprec, nullptr, 0, ctx->stream);
+        return launch_assemble(ctx->evR, action_ev_format(ctx->prec), ctx->csr_ptr, ctx->csr_idx,
+                               ctx->fixed, v, 1, ctx->Nx, ctx->d, ctx->ENP, y, ctx->vprec, nullptr,
+                               0, ctx->stream);
     }));
     return TMOP_OK;
 }

@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace tmop {
 
 // Bit-level conversions between double and float pairs that use only the
@@ -227,6 +229,38 @@ __device__ __forceinline__ void asm_renorm(df &a) { a = norm(a); }
 template <class RO> __device__ __forceinline__ RO asm_out(double a) { return RO(a); }
 template <class RO> __device__ __forceinline__ RO asm_out(const df &a) { return RO(norm(a).h); }
 
+// Element vectors of the double-float Hessian action: each entry is the
+// (unnormalised) float pair of the element sum, stored in the 8 bytes of a
+// double slot.  The action kernels then run no FP64-unit conversion on their
+// output; the assembly sums the pairs in double-float (TwoSum of the high
+// words, low words and rounding errors in the low word, renormalised every 8
+// entries) and rounds once per DOF to double.
+template <class RV, class RC> struct EvPair { static constexpr bool value = false; };
+template <> struct EvPair<double, df> { static constexpr bool value = true; };
+template <> struct AsmAcc<df> { using T = df; };
+__device__ __forceinline__ void asm_add(df &a, const df &v) { acc_add(a, dprod{v.h, v.l}); }
+template <> __device__ __forceinline__ double asm_out<double>(const df &a)
+{
+    return (double)a.h + (double)a.l;
+}
+// entry loads of the assembly (read-only path; float pairs as one 8-byte load)
+__device__ __forceinline__ double ld_entry(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_entry(const float *p) { return __ldg(p); }
+__device__ __forceinline__ df ld_entry(const df *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return df(v.x, v.y);
+}
+__device__ __forceinline__ double ld_plain(const double *p) { return *p; }
+__device__ __forceinline__ float ld_plain(const float *p) { return *p; }
+__device__ __forceinline__ df ld_plain(const df *p)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return df(v.x, v.y);
+}
+
+
+
 // Conversions used by the templated kernels.
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(float v) { return (double)v; }
@@ -242,5 +276,31 @@ template <class R>
 __device__ __forceinline__ R from_d(double v) { return (R)v; }
 template <>
 __device__ __forceinline__ df from_d<df>(double v) { return df(v); }
+
+// Store of an action element-vector entry: the float pair (EvPair) or the
+// value rounded to RV.
+template <class RV, class RC>
+__device__ __forceinline__ void ev_store(RV *p, const RC &a)
+{
+    if constexpr (EvPair<RV, RC>::value)
+        *reinterpret_cast<float2 *>(p) = make_float2(a.h, a.l);
+    else if constexpr (std::is_same<RV, RC>::value)
+        *p = a;
+    else
+        *p = RV(to_d(a));
+}
+// *p += a on an action element-vector entry (terms added after the main
+// action kernel, before the assembly).
+template <class RV, class RC>
+__device__ __forceinline__ void ev_accum(RV *p, const RC &a)
+{
+    if constexpr (EvPair<RV, RC>::value) {
+        const float2 o = *reinterpret_cast<const float2 *>(p);
+        const df s = df(o.x, o.y) + a;
+        *reinterpret_cast<float2 *>(p) = make_float2(s.h, s.l);
+    } else {
+        *p = RV(to_d(*p) + to_d(a));
+    }
+}
 
 }  // namespace tmop

@@ -159,7 +159,8 @@ __device__ __forceinline__ void values_transpose(ElemCtx<C, R> &c, const R *f)
 
 // Transposed contractions of sA[(a*D + b)*NQD + q] (b = derivative
 // direction) and store of the element vector component a.
-template <class C, class R, class ROUT>
+// ACT: an action element vector (ev_store: float pairs for double-float).
+template <class C, class R, class ROUT, bool ACT = false>
 __device__ __forceinline__ void backward_component(const ElemParams &P, ElemCtx<C, R> &c,
                                                    ROUT *__restrict__ ev, int a)
 {
@@ -171,7 +172,10 @@ __device__ __forceinline__ void backward_component(const ElemParams &P, ElemCtx<
         bwd2<C, R>(c.B, c.G, Y0, Y0 + C::NQD, c.s1, c.su, c.tx, c.ty, c.valid);
     if (c.valid)
         for (int i = c.t; i < C::NP; i += C::TPE)
-            ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = ROUT(to_d(c.su[i]));
+            if constexpr (ACT)
+                ev_store(&ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i], c.su[i]);
+            else
+                ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i] = ROUT(to_d(c.su[i]));
 }
 
 // Iterate over this thread's quadrature points: (q1, q2) = (tx, ty), all q3.
@@ -686,7 +690,7 @@ k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__
         }
     });
     __syncthreads();
-    for (int a = 0; a < C::D; ++a) backward_component<C, RC, RV>(P, c, ev, a);
+    for (int a = 0; a < C::D; ++a) backward_component<C, RC, RV, true>(P, c, ev, a);
 }
 
 // ---------------------------------------------------------------- diagonal

@@ -120,8 +120,7 @@ k_limit_apply(ElemParams P, const RV *__restrict__ v, const double *__restrict__
         values_transpose<C, RC>(c, f);
         if (c.valid)
             for (int i = c.t; i < C::NP; i += C::TPE) {
-                RV &o = ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i];
-                o = RV(to_d(o) + to_d(c.su[i]));
+                ev_accum(&ev[(int64_t)a * P.E * C::NP + c.e * C::NP + i], c.su[i]);
             }
         __syncthreads();
     }

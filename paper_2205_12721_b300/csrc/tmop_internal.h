@@ -25,6 +25,16 @@ struct BatchArgs;
 // Arithmetic of the FP64-accuracy contractions (energy, gradient, setup).
 enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
 
+// Element-vector format of the double-float Hessian action (TMOP_FP64): float
+// pairs in 8-byte slots (dfloat.cuh, EvPair), an ev_prec of launch_assemble.
+enum { EV_DF_PAIR = 16 };
+// Element-vector format written by the Hessian action of a precision.
+inline int action_ev_format(int hess_precision)
+{
+    return hess_precision == TMOP_FP64 ? EV_DF_PAIR
+                                       : (hess_precision == TMOP_FP32 ? TMOP_FP32 : TMOP_FP64);
+}
+
 // Element-kernel launchers (one translation unit each).  Return the launch
 // error.  nblocks() is the grid size a launch over E elements uses.
 int64_t elem_blocks(int d, int p, int q, int64_t E);

@@ -51,7 +51,7 @@ __global__ void k_assemble(const RI *__restrict__ ev, const int32_t *__restrict_
         const int64_t t = __ldg(idx + j);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (a < D) asm_add(s[a], __ldg(ev + a * ENP + t));
+            if (a < D) asm_add(s[a], ld_entry(ev + a * ENP + t));
         if (((j - b) & 7) == 7)
 #pragma unroll
             for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
@@ -216,7 +216,7 @@ __global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *_
             const int64_t t = __ldg(idx + j);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                if (a < D) asm_add(s[a], __ldg(ev + a * ENP + t));
+                if (a < D) asm_add(s[a], ld_entry(ev + a * ENP + t));
             if (((j - b) & 7) == 7)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) asm_renorm(s[a]);
@@ -584,6 +584,10 @@ cudaError_t launch_assemble(const void *ev, int ev_prec, const int32_t *ptr, con
         k_assemble<float, float><<<g, VT, 0, s>>>((const float *)ev, ptr, idx, fixed,
                                                   (const float *)vfix, mode, Nx, D, ENP,
                                                   (float *)out, stop, k);
+    else if (ev_prec == EV_DF_PAIR && out_prec == TMOP_FP64)
+        k_assemble<df, double><<<g, VT, 0, s>>>((const df *)ev, ptr, idx, fixed,
+                                                (const double *)vfix, mode, Nx, D, ENP,
+                                                (double *)out, stop, k);
     else
         return cudaErrorInvalidValue;
     count_launch();
