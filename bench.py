@@ -40,8 +40,7 @@ MINRES_ITS = 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one action launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {("fp64", 7): 2.699e9, ("fp32", 4): 1.375e9,     # (precision, action variant)
-                 ("fp64", 13): 2.693e9, ("fp32", 12): 1.370e9}
+TRAFFIC_BYTES = {("fp64", 13): 2.691e9, ("fp32", 17): 1.366e9}     # (precision, action variant)
 PRECISION_LABEL = {"fp64": "fp64-class (double-float contractions, 48-bit significand)",
                    "fp32": "fp32-mixed (fp32 stored d2mu/dT2, action and MINRES; fp64 residual, "
                            "energy, det and line search)",
@@ -61,7 +60,9 @@ APPLY_VARIANT_NAME = {0: "sum-factorised register column", 1: "collocated, regis
                       13: "collocated, per-warp shared-memory column with aliased buffers, 8 warps/CTA, 24 warps/SM, L2 prefetch",
                       14: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 20 (FP32 32) warps/SM, L2 prefetch",
                       15: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 24 warps/SM, L2 prefetch",
-                      16: "collocated, per-warp shared-memory column with aliased buffers, 8 warps/CTA, 24 warps/SM"}
+                      16: "collocated, per-warp shared-memory column with aliased buffers, 8 warps/CTA, 24 warps/SM",
+                      17: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 24 warps/SM, input gathered up front",
+                      18: "collocated, per-warp shared-memory column with aliased buffers, 4 warps/CTA, 20 (FP32 32) warps/SM, input gathered up front"}
 
 
 def flops_apply_per_elem(d, ni, nq, ns, collocated=False):
@@ -794,9 +795,11 @@ def run_split(args, rank, world, local_rank):
 def run_autotune(args):
     """The autotuner over the Hessian-action kernel variants: for every
     configuration with more than one variant (3D, p = 1..4, n_q = p+1 and p+2
-    with n_q^2 <= 32) and every precision, a mesh of the benchmark family whose
-    stored data exceeds L2 (~1.2 GB), tmop_autotune (CUDA events, 10 launches
-    per variant); prints the measured times and the chosen variant per
+    with n_q^2 <= 32; or those of --autotune-configs) and every precision, a
+    mesh of the benchmark family whose stored data exceeds L2 (~1.2 GB, or
+    --autotune-n-e elements per side), tmop_autotune (CUDA events, 10 launches
+    per variant) repeated --autotune-passes times, the per-variant minimum of
+    the passes; prints the measured times and the chosen variant per
     configuration, the rows of autotune_table.json."""
     import torch
     from paper_2205_12721_b300 import capi, meshgen
@@ -804,19 +807,25 @@ def run_autotune(args):
     hbm = measured_peaks().get("hbm_gbs")
     precs = {"fp64": capi.FP64, "fp32": capi.FP32, "fp64-native": capi.FP64_NATIVE}
     rows = []
+    sel = [tuple(int(v) for v in c.split(":")) for c in args.autotune_configs]
     for p in (1, 2, 3, 4):
         for nq in (p + 1, p + 2):
-            if capi.tmop_apply_variants(3, p, nq) <= 1:
+            if capi.tmop_apply_variants(3, p, nq) <= 1 or (sel and (p, nq) not in sel):
                 continue
             for name in args.autotune_precisions:
                 rsz = 4 if name == "fp32" else 8
                 per_el = 45 * nq ** 3 * rsz
-                n = max(8, int(round((args.autotune_bytes / per_el) ** (1.0 / 3.0))))
+                n = args.autotune_n_e or max(8, int(round((args.autotune_bytes / per_el) ** (1.0 / 3.0))))
                 m = meshgen.config_mesh(3, n_e=n, order=p)
                 gm = TmopMesh.from_structured(m, capi.METRIC_303, nq1d=nq, precision=name)
                 x = torch.from_numpy(m.x).cuda()
                 gm.hessian_setup(x)
-                best, ms = capi.tmop_autotune(gm.ctx, 10)
+                ms = None
+                for _ in range(args.autotune_passes):
+                    _, t = capi.tmop_autotune(gm.ctx, 10)
+                    ms = t if ms is None else [min(a, b) for a, b in zip(ms, t)]
+                best = min(range(len(ms)), key=lambda i: ms[i])
+                capi.tmop_set_apply_variant(3, p, nq, precs[name], best)
                 gm.close()
                 byts = bytes_apply(m.num_elems, m.ndof, 3, p + 1, nq, 45, rsz)
                 rows.append({"d": 3, "p": p, "nq": nq, "precision": name, "prec": precs[name],
@@ -868,6 +877,11 @@ def main():
     ap.add_argument("--autotune-precisions", dest="autotune_precisions", nargs="+",
                     default=["fp64", "fp32", "fp64-native"])
     ap.add_argument("--autotune-bytes", dest="autotune_bytes", type=float, default=1.2e9)
+    ap.add_argument("--autotune-n-e", dest="autotune_n_e", type=int, default=0,
+                    help="elements per side of the autotuner's meshes (default: from --autotune-bytes)")
+    ap.add_argument("--autotune-configs", dest="autotune_configs", nargs="*", default=[],
+                    help="p:nq pairs to tune (default: all with more than one variant)")
+    ap.add_argument("--autotune-passes", dest="autotune_passes", type=int, default=1)
     ap.add_argument("--traffic", type=float, default=None,
                     help="override the ncu dram bytes per launch of the apply kernel")
     args = ap.parse_args()

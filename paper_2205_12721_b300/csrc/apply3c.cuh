@@ -33,7 +33,10 @@
 //               at the time: rows 6-8 (component 2) during the forward pass,
 //               rows 0-2 (component 0) during the transposed pass, which
 //               frees 2 x BUF values per element of shared memory for more
-//               resident CTAs.
+//               resident CTAs;
+//   GA          the input values of all three components are gathered into
+//               registers before the forward pass (one exposed gather latency
+//               per element instead of three).
 #pragma once
 
 #include <type_traits>
@@ -61,12 +64,34 @@ struct Apply3cShape {
     static constexpr int BUF = C::NQ * C::NQ * C::NQ;          // >= NP, NQ NI^2, NQ^2 NI
     static constexpr int NPL = (C::NP + TPE - 1) / TPE;        // map entries per lane
     static constexpr int TABN = C::NQ * C::NI + C::NQ * C::NQ;
-    // the two buffers of a warp's elements fit in three column rows of the warp
+    // Stride of the two buffers of consecutive elements of a warp, in values of
+    // R: every stage reads or writes one n_q x n_q plane per element, at the
+    // same plane offset for all lanes, so elements whose planes start
+    // span = TPE * sizeof(R) / 4 banks apart use disjoint banks when
+    // EPW * span <= 32 (no two-way conflict between the elements of a warp).
+    template <class R>
+    static constexpr int es_padded()
+    {
+        constexpr int w = (int)(sizeof(R) / 4);
+        constexpr int span = TPE * w;
+        if (span >= 32 || EPW == 1) return 2 * BUF;
+        int es = 2 * BUF;
+        while ((es * w) % 32 != span % 32) ++es;
+        return es;
+    }
+    // AL: the buffers of a warp's elements lie in three column rows of the
+    // warp (3 * NQ * 32 values); padded stride where that still fits
+    template <class R>
+    static constexpr int es(bool al)
+    {
+        return (!al || 2 * BUF + (EPW - 1) * es_padded<R>() <= 3 * C::NQ * 32) ? es_padded<R>()
+                                                                              : 2 * BUF;
+    }
     static_assert(2 * EPW * BUF <= 3 * C::NQ * 32, "aliased buffers");
     template <class R>
     static constexpr size_t bytes(bool sc, bool al = false)
     {
-        return sizeof(R) * (size_t)(((TABN + 1) & ~1) + (al ? 0 : EPB * 2 * BUF) +
+        return sizeof(R) * (size_t)(((TABN + 1) & ~1) + (al ? 0 : EPB * es<R>(false)) +
                                     (sc ? 9 * C::NQ * NT : 0));
     }
 };
@@ -88,6 +113,26 @@ __device__ __forceinline__ df ld_stream(const df *p)
 }
 __device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_stream(const double *p) { return __ldcs(p); }
+// Two consecutive stored values (an entry pair of the stored layout; p is
+// aligned to their combined size).
+__device__ __forceinline__ void ld_stream2(const df *p, df &a, df &b)
+{
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    a = df(v.x, v.y);
+    b = df(v.z, v.w);
+}
+__device__ __forceinline__ void ld_stream2(const float *p, float &a, float &b)
+{
+    const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_stream2(const double *p, double &a, double &b)
+{
+    const double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
+    a = v.x;
+    b = v.y;
+}
 
 // Conversions of the gathered input and of the element-vector output (the
 // FP64-unit conversions measured faster here than the bit-level ones).
@@ -128,7 +173,7 @@ __host__ __device__ constexpr int pcol9(int k) { return prow9(k) + (k - pidx<9>(
 // issued before the multiply-adds of chunk j; the same arithmetic in the same
 // order as the plain point loop.
 template <class C, class RV, class RC, int WPB, bool SC, bool ROLL, int MINB, bool PFN = false,
-          bool PIPE = false, bool AL = false>
+          bool PIPE = false, bool AL = false, bool GA = false>
 __global__ void __launch_bounds__(Apply3cShape<C, WPB>::NT, MINB)
 k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
           const int *__restrict__ stop_iter, int k, BatchArgs BA, int64_t ntiles,
@@ -180,12 +225,13 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     // SC: the dA / Y columns of every thread, [(r * NQ + q3) * NT + thread],
     // or with AL blocked per warp, [warp][(r * NQ + q3) * 32 + lane]
     constexpr int CST = AL ? 32 : S::NT;                    // stride of a column row
-    RC *cs = Bs + ((S::TABN + 1) & ~1) + (AL ? warp * 9 * NQ * 32 : S::EPB * 2 * BUF);
+    RC *cs = Bs + ((S::TABN + 1) & ~1) + (AL ? warp * 9 * NQ * 32 : S::EPB * S::template es<RC>(false));
     const int ci = AL ? lane : threadIdx.x;                 // the thread's column
     // AL: the buffers of the forward pass in rows 6-8 (component 2), of the
     // transposed pass in rows 0-2 (component 0)
-    RC *b0 = AL ? cs + 6 * NQ * 32 + (act ? slot : 0) * 2 * BUF
-                : Bs + ((S::TABN + 1) & ~1) + el * 2 * BUF;
+    constexpr int ES = S::template es<RC>(AL);              // buffer stride per element
+    RC *b0 = AL ? cs + 6 * NQ * 32 + (act ? slot : 0) * ES
+                : Bs + ((S::TABN + 1) & ~1) + el * ES;
     RC *b1 = b0 + BUF;
     const int64_t e = e0 + (act ? slot : 0);
     const bool valid = act && e < P.E;
@@ -194,6 +240,16 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     for (int j = 0; j < S::NPL; ++j) {
         const int i = t + j * S::TPE;
         m[j] = (valid && i < NP) ? P.map[e * NP + i] : 0;
+    }
+    RV gv[GA ? 3 : 1][S::NPL];
+    if (GA) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < S::NPL; ++j) {
+                const int i = t + j * S::TPE;
+                gv[GA ? c : 0][j] = (valid && i < NP) ? v[c * P.Nx + m[j]] : RV(0);
+            }
     }
 
     RC col[SC ? 1 : 9][NQ];                                 // dA_{cb} then Y_{cb} at (tx, ty, q3)
@@ -205,7 +261,17 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
 #pragma unroll
         for (int j = 0; j < S::NPL; ++j) {
             const int i = t + j * S::TPE;
-            if (valid && i < NP) b0[i] = cvt_in<RC>(v[c * P.Nx + m[j]]);
+            if (valid && i < NP) {
+                if constexpr (GA) {
+                    RV x = gv[0][j];                        // c is a loop variable: unrolled select
+#pragma unroll
+                    for (int cc = 1; cc < 3; ++cc)
+                        if (cc == c) x = gv[GA ? cc : 0][j];
+                    b0[i] = cvt_in<RC>(x);
+                } else {
+                    b0[i] = cvt_in<RC>(v[c * P.Nx + m[j]]);
+                }
+            }
         }
         __syncwarp();
         if (valid && ty < NI) {                             // i1 -> q1
@@ -301,16 +367,36 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
         __syncwarp();                                       // b0 is reused by the next gather
     }
 
-    // ---- pointwise: Y = H : dA with the symmetric-packed stored data
+    // ---- pointwise: Y = H : dA with the symmetric-packed stored data; the
+    // packed entries k = 0..NS-1 of a point in order, row 0 starting every sum
+    static_assert(NS == 45, "3D packed data");
+    const RC *He = H + e * (int64_t)C::HST;
+    const int pt = ty * NQ + tx;                            // the thread's point of a q3 plane
+    // the terms of packed entry KK (row r <= column s, value h)
+    auto term = [](auto KK, const RC &h, const RC *d, RC *y) {
+        constexpr int kk = decltype(KK)::value;
+        constexpr int r = prow9(kk), sc = pcol9(kk);
+        if constexpr (r == 0) {
+            y[sc] = mul1(h, d[0]);
+            if constexpr (sc > 0) acc_add(y[0], h * d[sc]);
+        } else {
+            acc_add(y[sc], h * d[r]);
+            if constexpr (sc != r) acc_add(y[r], h * d[sc]);
+        }
+    };
+    // L2 prefetch of the stored values of point q (one line per entry pair)
+    auto prefetch_point = [&](int q) {
+#pragma unroll
+        for (int g = 0; g <= C::NPR; ++g)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(He + C::hoff(2 * g, q)));
+    };
     if (PIPE && SC && valid) {
-        static_assert(NS == 45, "3D packed data");
         constexpr int CH = 9, NCH = 5;                  // 45 = 5 chunks of 9 per point
         constexpr int NJ = NQ * NCH;
         constexpr int UJ = (NQ % 2 == 0) ? 2 * NCH : NJ;   // chunks per unrolled body
-        const RC *He = H + e * (int64_t)(NS * NQD) + (ty * NQ + tx);
         RC hb0[CH], hb1[CH];                            // the two chunk buffers
 #pragma unroll
-        for (int t2 = 0; t2 < CH; ++t2) hb0[t2] = ld_stream(He + t2 * NQD);
+        for (int t2 = 0; t2 < CH; ++t2) hb0[t2] = ld_stream(He + C::hoff(t2, pt));
 #pragma unroll 1
         for (int j0 = 0; j0 < NJ; j0 += UJ) {
             RC d[9], y[9];
@@ -322,14 +408,10 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                 RC *nxt = (jj & 1) ? hb0 : hb1;
                 const int q3 = j0 / NCH + jj / NCH;
                 if (j0 + jj + 1 < NJ) {                 // loads of the next chunk
-                    const RC *Hn = He + (j0 / NCH + (jj + 1) / NCH) * NQ * NQ + c1 * CH * NQD;
+                    const int qn = (j0 / NCH + (jj + 1) / NCH) * NQ * NQ + pt;
 #pragma unroll
-                    for (int t2 = 0; t2 < CH; ++t2) nxt[t2] = ld_stream(Hn + t2 * NQD);
-                    if (PFN && c == 0 && q3 + 1 < NQ) {
-#pragma unroll
-                        for (int s2 = 0; s2 < NS; ++s2)
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(He + (q3 + 1) * NQ * NQ + s2 * NQD));
-                    }
+                    for (int t2 = 0; t2 < CH; ++t2) nxt[t2] = ld_stream(He + C::hoff(c1 * CH + t2, qn));
+                    if (PFN && c == 0 && q3 + 1 < NQ) prefetch_point((q3 + 1) * NQ * NQ + pt);
                 }
                 if constexpr (c == 0) {
 #pragma unroll
@@ -337,16 +419,7 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                 }
                 static_for<CH>([&](auto T2) {
                     constexpr int t2 = decltype(T2)::value;
-                    constexpr int kk = c * CH + t2;     // packed entry
-                    constexpr int r = prow9(kk), sc = pcol9(kk);
-                    const RC h = cur[t2];
-                    if constexpr (r == 0) {             // row 0 starts every sum
-                        y[sc] = mul1(h, d[0]);
-                        if constexpr (sc > 0) acc_add(y[0], h * d[sc]);
-                    } else {
-                        acc_add(y[sc], h * d[r]);
-                        if constexpr (sc != r) acc_add(y[r], h * d[sc]);
-                    }
+                    term(std::integral_constant<int, c * CH + t2>{}, cur[t2], d, y);
                 });
                 if constexpr (c == NCH - 1) {
 #pragma unroll
@@ -355,33 +428,22 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
             });
         }
     } else if (valid) {
-        const RC *He = H + e * (int64_t)(NS * NQD) + (ty * NQ + tx);
         // ROLL (shared-memory columns only): one copy of the point body
 #pragma unroll(SC && ROLL ? 1 : NQ)
         for (int q3 = 0; q3 < NQ; ++q3) {
-            const RC *Hq = He + q3 * NQ * NQ;
-            if (PFN && q3 + 1 < NQ) {
-#pragma unroll
-                for (int s = 0; s < NS; ++s)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(Hq + NQ * NQ + s * NQD));
-            }
+            const int q = q3 * NQ * NQ + pt;
+            if (PFN && q3 + 1 < NQ) prefetch_point(q + NQ * NQ);
             RC d[9], y[9];
 #pragma unroll
             for (int r = 0; r < 9; ++r) d[r] = COLW(r, q3);
-#pragma unroll
-            for (int s = 0; s < 9; ++s) {                   // row r = 0 starts every sum
-                const RC h = ld_stream(Hq + pidx<9>(0, s) * NQD);
-                y[s] = mul1(h, d[0]);
-                if (s > 0) acc_add(y[0], h * d[s]);
-            }
-#pragma unroll
-            for (int r = 1; r < 9; ++r)
-#pragma unroll
-                for (int s = r; s < 9; ++s) {
-                    const RC h = ld_stream(Hq + pidx<9>(r, s) * NQD);
-                    acc_add(y[s], h * d[r]);
-                    if (s != r) acc_add(y[r], h * d[s]);
-                }
+            static_for<C::NPR>([&](auto G) {            // entries 2g, 2g+1: one pair load
+                constexpr int g = decltype(G)::value;
+                RC h0, h1;
+                ld_stream2(He + C::hoff(2 * g, q), h0, h1);
+                term(std::integral_constant<int, 2 * g>{}, h0, d, y);
+                term(std::integral_constant<int, 2 * g + 1>{}, h1, d, y);
+            });
+            term(std::integral_constant<int, NS - 1>{}, ld_stream(He + C::hoff(NS - 1, q)), d, y);
 #pragma unroll
             for (int r = 0; r < 9; ++r) COLW(r, q3) = y[r];
         }
@@ -389,7 +451,7 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
 
     // ---- transposed: D^T along each direction, then B^T along q3, q2, q1
     if (AL) {
-        b0 = cs + (act ? slot : 0) * 2 * BUF;
+        b0 = cs + (act ? slot : 0) * ES;
         b1 = b0 + BUF;
     }
 #pragma unroll 1

@@ -13,25 +13,25 @@ struct ApplyTuned {
 
 static const ApplyTuned kApplyTuned[] = {
     {3, 1, 2, 0, 14},
-    {3, 1, 2, 1, 2},
-    {3, 1, 2, 2, 2},
-    {3, 1, 3, 0, 11},
-    {3, 1, 3, 1, 1},
+    {3, 1, 2, 1, 4},
+    {3, 1, 2, 2, 1},
+    {3, 1, 3, 0, 3},
+    {3, 1, 3, 1, 4},
     {3, 1, 3, 2, 0},
-    {3, 2, 3, 0, 15},
-    {3, 2, 3, 1, 10},
-    {3, 2, 3, 2, 1},
-    {3, 2, 4, 0, 13},
-    {3, 2, 4, 1, 12},
+    {3, 2, 3, 0, 18},
+    {3, 2, 3, 1, 17},
+    {3, 2, 3, 2, 2},
+    {3, 2, 4, 0, 18},
+    {3, 2, 4, 1, 2},
     {3, 2, 4, 2, 1},
     {3, 3, 4, 0, 13},
-    {3, 3, 4, 1, 12},
-    {3, 3, 4, 2, 6},
-    {3, 3, 5, 0, 9},
-    {3, 3, 5, 1, 12},
+    {3, 3, 4, 1, 17},
+    {3, 3, 4, 2, 2},
+    {3, 3, 5, 0, 5},
+    {3, 3, 5, 1, 17},
     {3, 3, 5, 2, 0},
-    {3, 4, 5, 0, 14},
-    {3, 4, 5, 1, 12},
+    {3, 4, 5, 0, 7},
+    {3, 4, 5, 1, 17},
     {3, 4, 5, 2, 6},
 };
 

@@ -724,7 +724,7 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     SCK(cudaMemcpyAsync(c->tabf, tabf.data(), sizeof(float) * tabn, cudaMemcpyHostToDevice, c->stream));
     // stored Hessian data, element vectors, reductions, work vectors
     // padded to a 256-byte multiple: the action kernels prefetch whole 16-byte lines
-    STRY(c->alloc_raw(&c->H, ((c->rsz * (size_t)c->E * c->ns * c->nqd + 255) / 256) * 256 + 256));
+    STRY(c->alloc_raw(&c->H, ((c->rsz * (size_t)c->E * h_stride(c->ns, c->nqd) + 255) / 256) * 256 + 256));
     STRY(c->alloc(&c->ev64, (size_t)c->d * c->ENP));
     if (c->vprec == TMOP_FP32) STRY(c->alloc_raw(&c->evR, 4 * (size_t)c->d * c->ENP));
     else c->evR = c->ev64;

@@ -31,7 +31,7 @@ int apply_variant_count(int d, int p, int q)
 {
     switch (TMOP_KEY(d, p, q)) {
 #define CASE(D_, P_, Q_) \
-    case TMOP_KEY(D_, P_, Q_): return (D_ == 3 && Q_ * Q_ <= 32) ? 17 : 1;
+    case TMOP_KEY(D_, P_, Q_): return (D_ == 3 && Q_ * Q_ <= 32) ? 19 : 1;
         TMOP_CONFIGS(CASE)
 #undef CASE
         default: return 0;

@@ -23,6 +23,8 @@
 //  14  as 11 with the L2 prefetch
 //  15  as 12 with the L2 prefetch
 //  16  as 13 without the L2 prefetch
+//  17  as 12, the three input components gathered into registers up front
+//  18  as 11, the same gather
 #pragma once
 
 #include <type_traits>
@@ -53,7 +55,7 @@ static const ColTab<RC, NI, NQ> &coltab()
 // double-float / FP64, 24 for FP32, with rolled shared-memory columns; none
 // otherwise).
 template <class C, class RV, class RC, int WPB, bool SC, bool ROLL = true, bool PFN = false,
-          bool PIPE = false, bool AL = false, int RW = 0>
+          bool PIPE = false, bool AL = false, int RW = 0, bool GA = false>
 static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV *ev, const int *stop,
                                int k, cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
@@ -64,7 +66,7 @@ static cudaError_t run_apply3c(const ElemParams &P, const RV *v, const RC *H, RV
                                : (P.E + S::EPB - 1) / S::EPB;
     if (nb == 0) return cudaSuccess;
     const size_t bytes = S::template bytes<RC>(SC, AL);
-    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN, PIPE, AL>;
+    auto kern = k_apply3c<C, RV, RC, WPB, SC, ROLL, MINB, PFN, PIPE, AL, GA>;
     cudaError_t e = prepare(kern, bytes);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nb, S::NT, bytes, s>>>(P, v, H, ev, stop, k, B, ntiles, coltab<RC, C::NI, C::NQ>());
@@ -112,7 +114,7 @@ static cudaError_t run_apply_legacy(const ElemParams &P, const RV *v, const RC *
 template <class C>
 constexpr int apply_variant_count()
 {
-    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 17 : 1;
+    return (C::D == 3 && C::NQ * C::NQ <= 32) ? 19 : 1;
 }
 
 template <class C, class RV, class RC>
@@ -138,6 +140,8 @@ static cudaError_t run_apply(const ElemParams &P, const RV *v, const RC *H, RV *
             case 14: return run_apply3c<C, RV, RC, 4, true, true, true, false, true, F32 ? 32 : 20>(P, v, H, ev, stop, k, s, B, ntiles);
             case 15: return run_apply3c<C, RV, RC, 4, true, true, true, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
             case 16: return run_apply3c<C, RV, RC, 8, true, true, false, false, true, 24>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 17: return run_apply3c<C, RV, RC, 4, true, true, false, false, true, 24, true>(P, v, H, ev, stop, k, s, B, ntiles);
+            case 18: return run_apply3c<C, RV, RC, 4, true, true, false, false, true, F32 ? 32 : 20, true>(P, v, H, ev, stop, k, s, B, ntiles);
             default: break;
         }
     }

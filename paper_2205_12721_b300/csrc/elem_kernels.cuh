@@ -460,7 +460,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
     prologue<C, RS>(P, tile, smem, c);
     forward_geometry<C, RS>(P, c, x);
 
-    RH *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    RH *He = H + c.e * (int64_t)C::HST;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
         if (P.target != TGT_IDENTITY) {
@@ -479,7 +479,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                                      &tauw);
             if (!(tau > 0.0) || !(ws > 0.0)) {
 #pragma unroll
-                for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0f);
+                for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0f);
                 return;
             }
             const double sc = cq * iws * iws;
@@ -538,7 +538,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                             acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
                         }
                     }
-                    He[pidx<C::DD>(r, s) * C::NQD + q] = store_dw<RH>(norm(k));
+                    He[C::hoff(pidx<C::DD>(r, s), q)] = store_dw<RH>(norm(k));
                 }
             return;
         }
@@ -553,7 +553,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
             point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
             if (!(tau > 0.0) || !(ws > 0.0)) {
 #pragma unroll
-                for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0f);
+                for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0f);
                 return;
             }
             const double I2 = i2_dw(Td, Cd, I1w, g2w, TtTw, TTtw);
@@ -600,7 +600,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                     if (a == cc) acc_add(k, m2 * TtTw[e * 3 + b]);
                     acc_add(k, m2 * to_df(Td[a * 3 + e] * Td[cc * 3 + b]));
                     if (b == e) acc_add(k, m2 * TTtw[a * 3 + cc]);
-                    He[pidx<9>(r, s) * C::NQD + q] = store_dw<RH>(norm(k));
+                    He[C::hoff(pidx<9>(r, s), q)] = store_dw<RH>(norm(k));
                 }
             return;
         }
@@ -611,7 +611,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         invariants<C::D>(T, I1, tau, I2, Cf);
         if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points store 0
 #pragma unroll
-            for (int s = 0; s < C::NS; ++s) He[s * C::NQD + q] = RH(0.0);
+            for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0);
             return;
         }
         Inv v;
@@ -623,7 +623,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
             for (int r = 0; r < C::DD; ++r)
 #pragma unroll
                 for (int s = r; s < C::DD; ++s)
-                    He[pidx<C::DD>(r, s) * C::NQD + q] =
+                    He[C::hoff(pidx<C::DD>(r, s), q)] =
                         from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
         } else {
             double u[C::DD], w[C::DD];
@@ -644,7 +644,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                         if (C::D == 2) k += ft * ((a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0));
                         else k += ft * eps3(a, cc) * eps3(b, e) * T[(3 - a - cc) * 3 + (3 - b - e)];
                     }
-                    He[pidx<C::DD>(r, s) * C::NQD + q] = from_db<RH>(k);
+                    He[C::hoff(pidx<C::DD>(r, s), q)] = from_db<RH>(k);
                 }
         }
     });
@@ -674,13 +674,13 @@ k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__
     prologue<C, RC>(P, tile, smem, c);
     for (int a = 0; a < C::D; ++a) forward_component<C, RC, RV>(P, c, v, a, false);
 
-    const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    const RC *He = H + c.e * (int64_t)C::HST;
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
         RC dA[C::DD], h[C::NS];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) dA[r] = c.sA[r * C::NQD + q];
 #pragma unroll
-        for (int s = 0; s < C::NS; ++s) h[s] = He[s * C::NQD + q];
+        for (int s = 0; s < C::NS; ++s) h[s] = He[C::hoff(s, q)];
 #pragma unroll
         for (int r = 0; r < C::DD; ++r) {
             RC y = 0;
@@ -716,7 +716,7 @@ k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev, BatchArgs BA
         tbl[2][i] = prod(c.G[i], c.G[i]);
     }
     __syncthreads();
-    const RC *He = H + c.e * (int64_t)(C::NS * C::NQD);
+    const RC *He = H + c.e * (int64_t)C::HST;
     if constexpr (C::D == 3) {
         // The six (b <= e) pairs of each component a in one pass per
         // contraction stage (3 barriers per component): the thread's q3
@@ -733,11 +733,11 @@ k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev, BatchArgs BA
 #pragma unroll
                 for (int p = 0; p < 6; ++p) {
                     const RC *T3 = tbl[(PB[p] == 2) + (PE[p] == 2)];
-                    const RC *Hp = He + pidx<C::DD>(a * 3 + PB[p], a * 3 + PE[p]) * C::NQD;
+                    const int hs = pidx<C::DD>(a * 3 + PB[p], a * 3 + PE[p]);
                     RC col[NQ];
 #pragma unroll
                     for (int q3 = 0; q3 < NQ; ++q3) {
-                        const RC v = Hp[(q3 * NQ + c.ty) * NQ + c.tx];
+                        const RC v = He[C::hoff(hs, (q3 * NQ + c.ty) * NQ + c.tx)];
                         col[q3] = PB[p] == PE[p] ? v : twice(v);
                     }
 #pragma unroll
@@ -795,7 +795,7 @@ k_diag(ElemParams P, const RC *__restrict__ H, RV *__restrict__ ev, BatchArgs BA
                 const int r = a * C::D + b, s = a * C::D + e2;
                 const RC scale = (b == e2) ? RC(1.0) : RC(2.0);
                 for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int) {
-                    f[q] = prod(scale, He[pidx<C::DD>(r, s) * C::NQD + q]);
+                    f[q] = prod(scale, He[C::hoff(pidx<C::DD>(r, s), q)]);
                 });
                 __syncthreads();
                 const RC *T1 = tbl[(b == 0) + (e2 == 0)];

@@ -28,6 +28,9 @@ enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
 // Element-vector format of the double-float Hessian action (TMOP_FP64): float
 // pairs in 8-byte slots (dfloat.cuh, EvPair), an ev_prec of launch_assemble.
 enum { EV_DF_PAIR = 16 };
+// Values of stored d2mu/dT2 per element (Cfg::HST: ns entries at nqd points,
+// rounded up to a multiple of 4 for aligned entry-pair loads).
+inline int64_t h_stride(int ns, int nqd) { return ((int64_t)ns * nqd + 3) & ~(int64_t)3; }
 // Element-vector format written by the Hessian action of a precision.
 inline int action_ev_format(int hess_precision)
 {

@@ -35,7 +35,7 @@ def _restore_defaults():
 def test_every_variant_matches_oracle(p, nq, precision):
     prec, tol = PRECS[precision]
     n = capi.tmop_apply_variants(3, p, nq)
-    assert n == 17
+    assert n == 19
     metric = 303 if p % 2 else 302
     m = make_case(3, p, (5, 4, 3), seed=50 + p)
     om = oracle_mesh(m, metric, nq)
@@ -62,10 +62,10 @@ def test_every_variant_matches_oracle(p, nq, precision):
 def test_variant_table_api():
     assert capi.tmop_apply_variants(2, 2, 3) == 1
     assert capi.tmop_apply_variants(3, 4, 6) == 1          # 36 lanes: no collocated kernel
-    assert capi.tmop_apply_variants(3, 3, 4) == 17
+    assert capi.tmop_apply_variants(3, 3, 4) == 19
     assert capi.tmop_apply_variants(3, 5, 6) == 0          # unsupported
     with pytest.raises(capi.TmopError):
-        capi.tmop_set_apply_variant(3, 3, 4, capi.FP64, 17)
+        capi.tmop_set_apply_variant(3, 3, 4, capi.FP64, 19)
     with pytest.raises(capi.TmopError):
         capi.tmop_set_apply_variant(2, 2, 3, capi.FP64, 1)
     d0 = capi.tmop_get_apply_variant(3, 3, 4, capi.FP64)
@@ -81,13 +81,13 @@ def test_autotune_installs_the_fastest():
     x = dev(m.x)
     gm.hessian_setup(x)
     best, ms = capi.tmop_autotune(gm.ctx, 3)
-    assert len(ms) == 17 and all(t > 0 for t in ms)
+    assert len(ms) == 19 and all(t > 0 for t in ms)
     assert ms[best] == min(ms)
     assert capi.tmop_get_apply_variant(3, 3, 4, capi.FP64) == best
     gm.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 5, 7, 9, 10, 11, 12, 13, 16])
+@pytest.mark.parametrize("variant", [1, 2, 3, 5, 7, 9, 10, 11, 12, 13, 16, 17])
 def test_batched_trajectory_same_for_every_collocated_variant(variant):
     """Meshes of 3 x 3 x 2 = 18 elements against 8-element tiles: with 2 or 8
     warps per CTA a CTA covers half a tile or two tiles of different meshes."""
