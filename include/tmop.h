@@ -387,6 +387,19 @@ enum { TMOP_K_ENERGY = 0, TMOP_K_GRADIENT = 1, TMOP_K_HSETUP = 2, TMOP_K_APPLY =
  * launch on the context's stream, and reset the accumulated figures. */
 tmop_status tmop_profile_enable(tmop_ctx *ctx, int on);
 
+/* Run the MINRES iterations of tmop_newton_step as CUDA graphs (1, the
+ * default) or as separate launches (0).  A graph holds 4 iterations (the
+ * launches of an iteration read the iteration index from a device counter);
+ * one graph per phase of the work-vector rotation is captured on first use
+ * and replayed while its parameters (output vector, tolerance, kernel
+ * variant, limiting term) stay the same.  Graphs are not used while
+ * profiling is enabled or when the context's stream is the legacy default
+ * stream.  Results are the same either way (the same kernels in the same
+ * order). */
+tmop_status tmop_set_graphs(tmop_ctx *ctx, int on);
+/* Number of MINRES graph launches of this context so far (diagnostics). */
+int64_t tmop_graph_launches(const tmop_ctx *ctx);
+
 /* Accumulated device time (ms) and launch count of one kernel class since
  * profiling was enabled.  Synchronises the stream. */
 tmop_status tmop_profile_read(tmop_ctx *ctx, int kernel_class, double *total_ms,

@@ -42,7 +42,7 @@ __device__ __forceinline__ void apply3_body(ElemParams P, const RV *__restrict__
     v = static_cast<const RV *>(in);
     H = static_cast<const RC *>(aux);
     ev = static_cast<RV *>(out);
-    if (stop && *stop < k) return;
+    if (stop && *stop < iter_of(stop, k)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     RC *base = reinterpret_cast<RC *>(smem);
     const RC *__restrict__ tab = table_of<RC>(P);
@@ -279,7 +279,7 @@ k_apply3s(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
     v = static_cast<const RV *>(in);
     H = static_cast<const RC *>(aux);
     ev = static_cast<RV *>(out);
-    if (stop && *stop < k) return;
+    if (stop && *stop < iter_of(stop, k)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     RC *base = reinterpret_cast<RC *>(smem);
     const RC *__restrict__ tab = table_of<RC>(P);

@@ -219,7 +219,7 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
         if (BA.stop) stop = BA.stop + (int64_t)tt.x * BA.stop_stride;
         e0 = (int64_t)tt.y * C::EPB + g % C::EPB;
     }
-    if (stop && *stop < k) return;                          // MINRES already stopped
+    if (stop && *stop < iter_of(stop, k)) return;          // MINRES already stopped
 
     static_assert(!AL || SC, "aliased buffers need shared-memory columns");
     // SC: the dA / Y columns of every thread, [(r * NQ + q3) * NT + thread],

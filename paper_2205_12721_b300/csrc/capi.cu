@@ -20,6 +20,7 @@ namespace {
 
 thread_local std::string g_last_error;
 std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;          // this thread's launches (graph node counts)
 
 tmop_status fail(tmop_status st, const std::string &msg)
 {
@@ -53,7 +54,11 @@ struct ProfRec {
 }  // namespace
 
 namespace tmop {
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void count_launch(int n)
+{
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 }  // namespace tmop
 
@@ -87,6 +92,16 @@ struct tmop_ctx {
     void *kv[8] = {nullptr};     // v, R1, R2, Z, W1, W2, W3, spare
     MinresState *st = nullptr, *hst = nullptr;
     int check_every = 4;
+    // CUDA graphs of 4 MINRES iterations, one per phase of the 3-buffer
+    // rotation (the 4-buffer rotation returns to its start every 4 iterations)
+    bool graphs = true;
+    int64_t graph_launches = 0;
+    struct MinresGraph {
+        cudaGraphExec_t exec = nullptr;
+        const double *dx = nullptr;
+        double rtol = 0.0;
+        int fixed_its = 0, variant = -1, lim = 0, nodes = 0;
+    } mg[3];
     // limiting term
     double lim2 = 0.0;                 // 2 / delta^2, 0 when off
     double *x0 = nullptr, *lim_cq = nullptr, *part2 = nullptr;
@@ -522,29 +537,35 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
     // (R1, R2, Y) rotate; the first Y is Z
     void *Y = Z;
     Z = c->kv[7];
-    int k = 1;
-    for (; k <= max_it; ++k) {
-        TRY(apply_elements(c, v, &c->st->stop_iter, k));
+    // The launches of one iteration, all with k = -1: the kernels take the
+    // iteration from the device counter st->k, advanced by the first launch.
+    constexpr int KD = -1;
+    auto launch_iteration = [&]() -> tmop_status {
+        CK(launch_iter_next(c->st, c->stream));
+        TRY(apply_elements(c, v, &c->st->stop_iter, KD));
         if (fuse) {
             TRY(timed(c, TMOP_K_ASSEMBLE, "assemble + lanczos", [&] {
                 return launch_assemble_lanczos_a(c->evR, c->csr_ptr, c->csr_idx, c->fixed, c->Nx,
-                                                 c->d, c->ENP, Z, R1, v, c->st, pr, k, c->part, nb,
+                                                 c->d, c->ENP, Z, R1, v, c->st, pr, KD, c->part, nb,
                                                  c->stream);
             }));
         } else {
             TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {
                 return launch_assemble(c->evR, action_ev_format(c->prec), c->csr_ptr, c->csr_idx,
                                        c->fixed, nullptr, 1, c->Nx, c->d, c->ENP, Z, c->vprec,
-                                       &c->st->stop_iter, k, c->stream);
+                                       &c->st->stop_iter, KD, c->stream);
             }));
-            CK(launch_lanczos_a(Z, R1, v, c->st, pr, n, k, c->part, nb, c->stream));
+            CK(launch_lanczos_a(Z, R1, v, c->st, pr, n, KD, c->part, nb, c->stream));
         }
-        CK(launch_fin_alpha(c->part, nb, c->st, k, c->stream));
+        CK(launch_fin_alpha(c->part, nb, c->st, KD, c->stream));
         // Z holds y; new y = M^-1 y goes to the old R1
-        CK(launch_lanczos_b(Z, R2, c->minv, c->st, pr, n, k, R1, c->part, nb, c->stream));
-        CK(launch_fin_beta(c->part, nb, c->st, k, rtol, fixed_its, c->stream));
-        CK(launch_minres_update(v, W1, W2, W3, dx, R1, c->st, pr, n, k, c->stream));
-        // rotate: r1 <- r2, r2 <- y(Z), ynew lives in old R1 (consumed), freed old Y buffer
+        CK(launch_lanczos_b(Z, R2, c->minv, c->st, pr, n, KD, R1, c->part, nb, c->stream));
+        CK(launch_fin_beta(c->part, nb, c->st, KD, rtol, fixed_its, c->stream));
+        CK(launch_minres_update(v, W1, W2, W3, dx, R1, c->st, pr, n, KD, c->stream));
+        return TMOP_OK;
+    };
+    // rotate: r1 <- r2, r2 <- y(Z), ynew lives in old R1 (consumed), freed old Y buffer
+    auto rotate = [&] {
         void *oR1 = R1;
         R1 = R2;
         R2 = Z;
@@ -554,6 +575,60 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
         W1 = W2;
         W2 = W3;
         W3 = oW1;
+    };
+    // Blocks of 4 iterations as CUDA graphs (not with per-kernel profiling,
+    // whose events are host-side records, nor on the legacy stream); the graph
+    // of a phase is captured once and replayed while its parameters hold.
+    const bool graphs = c->graphs && !c->prof && c->stream != nullptr;
+    const int variant = apply_variant(c->d, c->p, c->nq, c->prec);
+    int k = 0;
+    while (k < max_it) {
+        if (graphs && max_it - k >= 4) {
+            tmop_ctx::MinresGraph &g = c->mg[(k / 4) % 3];
+            if (!g.exec || g.dx != dx || g.rtol != rtol || g.fixed_its != fixed_its ||
+                g.variant != variant || g.lim != (c->lim2 > 0.0)) {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+                cudaGraph_t graph = nullptr;
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                const int64_t l0 = t_launches;
+                tmop_status st = TMOP_OK;
+                for (int j = 0; j < 4 && st == TMOP_OK; ++j) {
+                    st = launch_iteration();
+                    rotate();
+                }
+                const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+                if (st != TMOP_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+                const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ei != cudaSuccess) {
+                    g.exec = nullptr;
+                    return cuda_fail(ei, "cudaGraphInstantiate");
+                }
+                g.dx = dx;
+                g.rtol = rtol;
+                g.fixed_its = fixed_its;
+                g.variant = variant;
+                g.lim = c->lim2 > 0.0;
+                g.nodes = (int)(t_launches - l0);
+                g_launches.fetch_sub(g.nodes, std::memory_order_relaxed);   // counted at launch
+                t_launches = l0;
+            } else {
+                for (int j = 0; j < 4; ++j) rotate();
+            }
+            CK(cudaGraphLaunch(g.exec, c->stream));
+            count_launch(g.nodes);
+            ++c->graph_launches;
+            k += 4;
+        } else {
+            TRY(launch_iteration());
+            rotate();
+            ++k;
+        }
         if (!fixed_its && (k % c->check_every == 0) && k < max_it) {
             CK(cudaMemcpyAsync(c->hst, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
@@ -596,6 +671,8 @@ void tmop_destroy(tmop_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &g : ctx->mg)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     for (void *q : ctx->allocs) cudaFree(q);
@@ -962,6 +1039,15 @@ tmop_status tmop_remap(tmop_ctx *ctx, const double *x0, const double *x1, const 
     if (st == TMOP_OK) g_last_error.clear();
     return st;
 }
+
+tmop_status tmop_set_graphs(tmop_ctx *ctx, int on)
+{
+    if (!ctx) return fail(TMOP_ERR_ARG, "NULL context");
+    ctx->graphs = on != 0;
+    return TMOP_OK;
+}
+
+int64_t tmop_graph_launches(const tmop_ctx *ctx) { return ctx ? ctx->graph_launches : 0; }
 
 tmop_status tmop_profile_enable(tmop_ctx *ctx, int on)
 {

@@ -655,7 +655,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
 // (double, float, or df with double vectors).  v is expected to be zero on
 // fixed DOFs (callers mask it first).  If stop_iter != nullptr and
 // *stop_iter < k the launch does nothing (MINRES iterations after
-// convergence).
+// convergence; k < 0: the device iteration counter, iter_of).
 template <class C, class RV, class RC>
 __global__ void __launch_bounds__(C::NT)
 k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__restrict__ ev,
@@ -668,7 +668,7 @@ k_apply(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *__
     v = static_cast<const RV *>(in);
     H = static_cast<const RC *>(aux);
     ev = static_cast<RV *>(out);
-    if (stop && *stop < k) return;
+    if (stop && *stop < iter_of(stop, k)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RC> c;
     prologue<C, RC>(P, tile, smem, c);

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(C::NT)
 k_limit_apply(ElemParams P, const RV *__restrict__ v, const double *__restrict__ cq,
               RV *__restrict__ ev, const int *__restrict__ stop_iter, int k)
 {
-    if (stop_iter && *stop_iter < k) return;
+    if (stop_iter && *stop_iter < iter_of(stop_iter, k)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     ElemCtx<C, RC> c;
     prologue<C, RC>(P, blockIdx.x, smem, c);

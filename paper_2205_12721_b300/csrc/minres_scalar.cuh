@@ -31,6 +31,7 @@ __device__ __forceinline__ void minres_start_scalars(MinresState *st, double bb)
     st->stop_iter = (b1 > 0.0) ? INT_MAX : 0;
     st->breakdown = 0;
     st->iters = 0;
+    st->k = 0;
 }
 
 // bb = (r_{k+1}, M^-1 r_{k+1}) of iteration k.

@@ -17,6 +17,12 @@
 
 namespace tmop {
 
+// Iteration index of a MINRES launch: k >= 0 as given, k < 0 the device
+// counter stored right after the stop iteration (MinresState::k: stop[1]), so
+// that an iteration's launches are the same in every iteration (CUDA graph
+// replay).
+__device__ __forceinline__ int iter_of(const int *stop, int k) { return k >= 0 ? k : stop[1]; }
+
 enum { MET_2 = 2, MET_7 = 7, MET_9 = 9, MET_55 = 55, MET_302 = 302, MET_303 = 303,
        MET_303_55 = 30355 };
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -97,10 +98,13 @@ void host_colloc_deriv(int nq, double *D);
 struct MinresState {
     double beta, beta_old, beta1, alpha, dbar, eps, eps_old, phibar, cs, sn, gamma, delta, phi;
     int stop_iter;   // first iteration after which nothing changes (INT_MAX while running)
+    int k;           // the current iteration (device counter; follows stop_iter)
     int breakdown;
     int iters;
-    int pad;
 };
+static_assert(offsetof(MinresState, k) == offsetof(MinresState, stop_iter) + sizeof(int),
+              "iter_of reads the iteration counter right after the stop iteration");
+
 
 // CG scalar state of one remap mass solve, kept on the device.
 struct CgState {
@@ -148,6 +152,8 @@ cudaError_t launch_assemble_lanczos_a(const void *ev, const int32_t *ptr, const 
                                       const void *r1, const void *v, const MinresState *st, int prec,
                                       int k, double *part, int nb, cudaStream_t s);
 cudaError_t launch_fin_alpha(const double *part, int nb, MinresState *st, int k, cudaStream_t s);
+// st->k += 1: the start of a MINRES iteration whose launches take k = -1.
+cudaError_t launch_iter_next(MinresState *st, cudaStream_t s);
 cudaError_t launch_lanczos_b(void *y, const void *r2, const void *minv, const MinresState *st,
                              int prec, int64_t n, int k, void *ynew, double *part, int nb,
                              cudaStream_t s);

@@ -9,6 +9,7 @@
 
 #include "dfloat.cuh"
 #include "minres_scalar.cuh"
+#include "tmop_device.cuh"
 #include "tmop_internal.h"
 
 namespace tmop {
@@ -39,7 +40,7 @@ __global__ void k_assemble(const RI *__restrict__ ev, const int32_t *__restrict_
                            const RO *__restrict__ vfix, int mode, int64_t Nx, int D, int64_t ENP,
                            RO *__restrict__ out, const int *__restrict__ stop, int k)
 {
-    if (stop && *stop < k) return;
+    if (stop && *stop < iter_of(stop, k)) return;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Nx) return;
     const int b = ptr[n], e = ptr[n + 1];
@@ -179,6 +180,7 @@ __global__ void k_lanczos_a(R *__restrict__ z, const R *__restrict__ r1, const R
                             const MinresState *__restrict__ st, int64_t n, int k,
                             double *__restrict__ part)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
     const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
@@ -203,6 +205,7 @@ __global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *_
                                      const R *__restrict__ r1, const R *__restrict__ v,
                                      const MinresState *__restrict__ st, int k, double *__restrict__ part)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
     const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
@@ -235,8 +238,11 @@ __global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *_
     if (threadIdx.x == 0) part[blockIdx.x] = dsum;
 }
 
+__global__ void k_iter_next(MinresState *st) { st->k += 1; }
+
 __global__ void k_fin_alpha(const double *__restrict__ part, int nb, MinresState *st, int k)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
     double s = 0.0;
@@ -251,6 +257,7 @@ __global__ void k_lanczos_b(R *__restrict__ y, const R *__restrict__ r2, const R
                             const MinresState *__restrict__ st, int64_t n, int k,
                             R *__restrict__ ynew, double *__restrict__ part)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
     const double c = st->alpha / st->beta;
@@ -270,6 +277,7 @@ __global__ void k_lanczos_b(R *__restrict__ y, const R *__restrict__ r2, const R
 __global__ void k_fin_beta(const double *__restrict__ part, int nb, MinresState *st, int k,
                            double rtol, int fixed_its)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
     double s = 0.0;
@@ -285,6 +293,7 @@ __global__ void k_minres_update(R *__restrict__ v, const R *__restrict__ w1, con
                                 const R *__restrict__ ynew, const MinresState *__restrict__ st,
                                 int64_t n, int k)
 {
+    if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     const double eo = st->eps_old, de = st->delta, ig = 1.0 / st->gamma, ph = st->phi;
     const double ib = (st->beta > 0.0) ? 1.0 / st->beta : 0.0;
@@ -708,6 +717,13 @@ cudaError_t launch_assemble_lanczos_a(const void *ev, const int32_t *ptr, const 
         k_assemble_lanczos_a<double, double><<<nb, VT, 0, s>>>(
             (const double *)ev, ptr, idx, fixed, Nx, D, ENP, (double *)y, (const double *)r1,
             (const double *)v, st, k, part);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iter_next(MinresState *st, cudaStream_t s)
+{
+    k_iter_next<<<1, 1, 0, s>>>(st);
     count_launch();
     return cudaGetLastError();
 }

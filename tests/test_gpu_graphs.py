@@ -1,0 +1,69 @@
+"""MINRES iterations as CUDA graphs (tmop_set_graphs): the Newton trajectory
+is bitwise the same with and without graphs (the same kernels in the same
+order, the iteration index taken from the device counter), with a
+tolerance-stopped MINRES (the host test between 4-iteration blocks), fixed
+iteration counts that are not a multiple of 4 (the tail runs as separate
+launches), FP32 vectors, the limiting term, and a change of kernel variant
+between steps (the graphs are captured again)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import dev, host, make_case
+from paper_2205_12721_b300 import capi
+from paper_2205_12721_b300.mesh_opt import TmopMesh
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(m, metric, graphs, precision, steps, stream, limit=0.0, variant_switch=False, **opts):
+    with torch.cuda.stream(stream):
+        gm = TmopMesh(m.dim, m.order, m.map, m.num_nodes, metric, fixed=m.fixed,
+                      precision=precision, stream=stream, limit_delta=limit,
+                      x0=m.x if limit > 0 else None)
+        capi.tmop_set_graphs(gm.ctx, graphs)
+        x = dev(m.x)
+        n0 = capi.tmop_launch_count()
+        reps = []
+        for i in range(steps):
+            if variant_switch and i == 1:
+                capi.tmop_set_apply_variant(m.dim, m.order, m.order + 1,
+                                            {"fp64": capi.FP64, "fp32": capi.FP32}[precision], 3)
+            reps.append(gm.newton_step(x, **opts))
+        stream.synchronize()
+        launches = capi.tmop_launch_count() - n0
+        out = (host(x), reps, launches, capi.tmop_graph_launches(gm.ctx))
+        gm.close()
+    if variant_switch:
+        capi.tmop_set_apply_variant(m.dim, m.order, m.order + 1,
+                                    {"fp64": capi.FP64, "fp32": capi.FP32}[precision], -1)
+    return out
+
+
+@pytest.mark.parametrize("d,p,metric,shape,precision,opts,limit,switch", [
+    (3, 2, 302, (4, 3, 3), "fp64", dict(minres_rtol=1e-8, minres_max_it=50), 0.0, False),
+    (3, 3, 303, (3, 3, 2), "fp64", dict(minres_rtol=0.0, minres_max_it=22, minres_fixed_its=True), 0.0, True),
+    (3, 2, 302, (4, 3, 3), "fp32", dict(minres_rtol=1e-6, minres_max_it=50), 0.0, False),
+    (2, 2, 2, (8, 8), "fp64", dict(minres_rtol=1e-8, minres_max_it=50), 0.05, False),
+], ids=["3d-p2-rtol", "3d-p3-fixed22-switch", "3d-p2-fp32", "2d-p2-limit"])
+def test_graphs_same_trajectory(d, p, metric, shape, precision, opts, limit, switch):
+    m = make_case(d, p, shape, seed=70 + p)
+    s = torch.cuda.Stream()
+    xg, rg, lg, ng = _run(m, metric, True, precision, 3, s, limit, switch, **opts)
+    xd, rd, ld, nd = _run(m, metric, False, precision, 3, s, limit, switch, **opts)
+    assert ng > 0 and nd == 0
+    assert np.array_equal(xg, xd)
+    for a, b in zip(rg, rd):
+        assert a["status"] == b["status"] == capi.OK
+        assert a["minres_iters"] == b["minres_iters"]
+        assert a["energy"] == b["energy"] and a["alpha"] == b["alpha"]
+    assert lg == ld                  # graph nodes counted as launches
+
+
+def test_graphs_not_used_on_the_legacy_stream():
+    m = make_case(3, 2, (3, 3, 2), seed=5)
+    gm = TmopMesh(m.dim, m.order, m.map, m.num_nodes, 302, fixed=m.fixed)
+    x = dev(m.x)
+    assert gm.newton_step(x)["status"] == capi.OK
+    assert capi.tmop_graph_launches(gm.ctx) == 0
+    gm.close()
