@@ -482,7 +482,8 @@ def run_batched(args):
         bs, slots = [], {}
         for p, js in sorted(groups.items()):
             b = TmopBatch(3, p, capi.METRIC_303_55, target=capi.TARGET_SIZE_FIELD, precision=prec,
-                          max_meshes=len(js), minres_max_it=50, newton_rtol=1e-10, newton_max_it=40)
+                          max_meshes=len(js), minres_max_it=50, newton_rtol=1e-10, newton_max_it=40,
+                          graphs=not args.no_graphs)
             for j in js:
                 slots[j] = (b, b.add_structured(work[j][0], h0=work[j][1]))
             bs.append(b)
@@ -734,7 +735,7 @@ def run_serving(args):
     for rate in args.rates:
         jobs = meshgen.serving_workload(args.n_jobs, rate=rate, n2=tuple(args.n2), n3=tuple(args.n3))
         srv = Server(int(args.budget_gb * (1 << 30)), precision=args.precision, newton_rtol=1e-6,
-                     newton_max_it=50, minres_max_it=50)
+                     newton_max_it=50, minres_max_it=50, graphs=not args.no_graphs)
         done = srv.run(jobs)
         srv.close()
         torch.cuda.synchronize()
@@ -868,6 +869,8 @@ def main():
     ap.add_argument("--remap-precisions", dest="remap_precisions", nargs="+",
                     default=["fp64", "fp64-native"])
     ap.add_argument("--n-meshes", dest="n_meshes", type=int, default=512)
+    ap.add_argument("--no-graphs", dest="no_graphs", action="store_true",
+                    help="batched / serving workloads: MINRES without CUDA graphs")
     ap.add_argument("--single-subset", dest="single_subset", type=int, default=32)
     ap.add_argument("--n-jobs", dest="n_jobs", type=int, default=2000)
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 50, 200])

@@ -453,6 +453,14 @@ enum { TMOP_FAULT_NONE = 0, TMOP_FAULT_MINRES_BREAKDOWN = 1 };
 tmop_status tmop_inject_fault(tmop_ctx *ctx, int fault);
 tmop_status tmop_batch_inject_fault(tmop_batch *b, int slot, int fault);
 
+/* MINRES iterations of tmop_batch_step as CUDA graphs of 4 iterations (1,
+ * the default) or separate launches (0), as tmop_set_graphs; a graph is
+ * captured again when the stepped subset of meshes, its tile tables or the
+ * kernel variant change.  No graphs on the legacy default stream. */
+tmop_status tmop_batch_set_graphs(tmop_batch *b, int on);
+/* Number of MINRES graph launches of this batch so far (diagnostics). */
+int64_t tmop_batch_graph_launches(const tmop_batch *b);
+
 /* ---- Kernel-variant autotuning (not part of the paper's method) ----------
  * The Hessian action (the dominant kernel, Sec. 3.4) has several kernel
  * variants for some configurations (3D with nq1d^2 <= 32): the

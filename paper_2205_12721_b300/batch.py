@@ -19,7 +19,7 @@ class TmopBatch:
     def __init__(self, dim, order, metric, nq1d=None, target=capi.TARGET_IDENTITY,
                  precision="fp64", max_meshes=64, minres_rtol=1e-8, minres_max_it=50,
                  minres_fixed_its=False, ls_factor=1.2, ls_max_halvings=20, newton_rtol=1e-10,
-                 newton_max_it=100, stream=None):
+                 newton_max_it=100, stream=None, graphs=True):
         self.dim, self.order = dim, order
         # each batch works on its own stream unless told otherwise, so that
         # batches stepped from different host threads overlap on the GPU
@@ -30,6 +30,7 @@ class TmopBatch:
                                    PRECISIONS[precision], max_meshes, opts, newton_rtol,
                                    newton_max_it)
         self.handle = capi.tmop_batch_create(self.desc, self.stream)
+        capi.tmop_batch_set_graphs(self.handle, graphs)
         self.ndof = {}
 
     def close(self):

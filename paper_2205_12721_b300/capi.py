@@ -35,6 +35,7 @@ EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_set_target_field", "tmop_set_remap_source", "tmop_remap", "tmop_det",
            "tmop_apply_variants", "tmop_get_apply_variant", "tmop_set_apply_variant",
            "tmop_autotune", "tmop_inject_fault", "tmop_batch_inject_fault",
+           "tmop_batch_set_graphs", "tmop_batch_graph_launches",
            "tmop_vec_lincomb", "tmop_vec_mul", "tmop_vec_dot", "tmop_vec_gather",
            "tmop_vec_scatter_add", "tmop_vec_jacobi")
 
@@ -130,6 +131,8 @@ def lib():
             "tmop_vec_jacobi": (I, [P, I64, P, P]),
             "tmop_vec_scatter_add": (I, [P, I64, P, P, P]),
             "tmop_batch_inject_fault": (I, [P, I, I]),
+            "tmop_batch_set_graphs": (I, [P, I]),
+            "tmop_batch_graph_launches": (I64, [P]),
             "tmop_hessian_setup": (I, [P, P]),
             "tmop_hessian_apply": (I, [P, P, P]),
             "tmop_hessian_diag": (I, [P, P]),
@@ -283,6 +286,14 @@ def tmop_inject_fault(ctx: int, fault: int):
 
 def tmop_batch_inject_fault(b: int, slot: int, fault: int):
     _check(lib().tmop_batch_inject_fault(b, slot, fault), "tmop_batch_inject_fault")
+
+
+def tmop_batch_set_graphs(b: int, on: bool = True):
+    _check(lib().tmop_batch_set_graphs(b, int(on)), "tmop_batch_set_graphs")
+
+
+def tmop_batch_graph_launches(b: int) -> int:
+    return int(lib().tmop_batch_graph_launches(b))
 
 
 def tmop_det(ctx: int, x, det):

@@ -124,7 +124,7 @@ __global__ void b_assemble(const BMesh *M, const int2 *tiles, int ev_role, int o
 {
     const int2 t = tiles[blockIdx.x];
     const BMesh &bm = M[t.x];
-    if (S && S[t.x].ms.stop_iter < k) return;
+    if (S && S[t.x].ms.stop_iter < (k >= 0 ? k : S[t.x].ms.k)) return;
     const int64_t n = (int64_t)t.y * NCH + threadIdx.x;
     const int64_t Nx = bm.P.Nx;
     if (n >= Nx) return;
@@ -226,6 +226,7 @@ __global__ void b_lanczos_a(const BMesh *M, const int2 *tiles, const BState *S, 
     const int2 t = tiles[blockIdx.x];
     const BMesh &bm = M[t.x];
     const MinresState &ms = S[t.x].ms;
+    if (k < 0) k = ms.k;                                   // device iteration counter
     if (ms.stop_iter < k) return;
     int64_t i0, i1;
     chunk_range(bm, t.y, i0, i1);
@@ -246,6 +247,7 @@ __global__ void b_lanczos_a(const BMesh *M, const int2 *tiles, const BState *S, 
 __global__ void b_fin_alpha(const BMesh *M, BState *S, const int *mlist, int k)
 {
     const int m = mlist[blockIdx.x];
+    if (k < 0) k = S[m].ms.k;
     if (S[m].ms.stop_iter < k) return;
     const BMesh &bm = M[m];
     const double *part = rp<double>(bm, ROLE_VPART);
@@ -263,6 +265,7 @@ __global__ void b_lanczos_b(const BMesh *M, const int2 *tiles, const BState *S, 
     const int2 t = tiles[blockIdx.x];
     const BMesh &bm = M[t.x];
     const MinresState &ms = S[t.x].ms;
+    if (k < 0) k = ms.k;
     if (ms.stop_iter < k) return;
     int64_t i0, i1;
     chunk_range(bm, t.y, i0, i1);
@@ -286,6 +289,7 @@ __global__ void b_fin_beta(const BMesh *M, BState *S, const int *mlist, int k, d
                            int fixed_its)
 {
     const int m = mlist[blockIdx.x];
+    if (k < 0) k = S[m].ms.k;
     if (S[m].ms.stop_iter < k) return;
     const BMesh &bm = M[m];
     const double *part = rp<double>(bm, ROLE_VPART);
@@ -303,6 +307,7 @@ __global__ void b_minres_update(const BMesh *M, const int2 *tiles, const BState 
     const int2 t = tiles[blockIdx.x];
     const BMesh &bm = M[t.x];
     const MinresState &ms = S[t.x].ms;
+    if (k < 0) k = ms.k;
     if (ms.stop_iter < k) return;
     int64_t i0, i1;
     chunk_range(bm, t.y, i0, i1);
@@ -318,6 +323,14 @@ __global__ void b_minres_update(const BMesh *M, const int2 *tiles, const BState 
         dx[i] += ph * wn;
         V[i] = (R)((double)YN[i] * ib);
     }
+}
+
+// S[m].ms.k += 1 for the meshes of the subset: the start of a MINRES
+// iteration whose launches take k = -1.
+__global__ void b_iter_next(BState *S, const int *mlist, int nm)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nm) S[mlist[j]].ms.k += 1;
 }
 
 template <class R>
@@ -458,6 +471,20 @@ struct tmop_batch {
     int nt_e = 0, nt_n = 0, nt_v = 0, nm = 0;
     int64_t bytes = 0;
     std::vector<int> fault;              // host-side fault of a mesh's next step (tests)
+    // the subset whose tables are on the device (valid while no mesh joins or leaves)
+    std::vector<int> cur;
+    bool cur_valid = false;
+    int64_t mesh_ver = 0;                // counts joins and leaves
+    // CUDA graphs of 4 MINRES iterations, one per phase of the 3-buffer rotation
+    bool graphs = true;
+    int64_t graph_launches = 0;
+    struct BGraph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<int> subset;
+        int64_t ver = -1;
+        const void *te = nullptr, *tn = nullptr, *tv = nullptr;
+        int variant = -1, nodes = 0;
+    } bg[3];
 };
 
 namespace {
@@ -532,6 +559,7 @@ tmop_status ensure(T **dptr, size_t *cap, size_t need)
 // Upload the tile tables of the meshes in ms (element, node and vector tiles).
 tmop_status set_subset(tmop_batch *b, const std::vector<int> &ms)
 {
+    if (b->cur_valid && ms == b->cur) return TMOP_OK;     // the tables are on the device
     size_t ne = 0, nn = 0, nv = 0;
     for (int m : ms) {
         ne += b->hM[m].ntile_e;
@@ -572,6 +600,8 @@ tmop_status set_subset(tmop_batch *b, const std::vector<int> &ms)
     b->nt_n = (int)nn;
     b->nt_v = (int)nv;
     b->nm = (int)ms.size();
+    b->cur = ms;
+    b->cur_valid = true;
     return TMOP_OK;
 }
 
@@ -638,31 +668,39 @@ tmop_status setup_and_minres(tmop_batch *b)
     count_launch(6);
     BCK(cudaGetLastError());
     const int max_it = D.solver.minres_max_it;
-    for (int k = 1; k <= max_it; ++k) {
+    // The launches of one iteration, all with k = -1: the kernels take the
+    // iteration from the per-mesh device counters, advanced by the first launch.
+    constexpr int KD = -1;
+    auto launch_iteration = [&]() -> tmop_status {
+        b_iter_next<<<blocks_for(b->nm, 128), 128, 0, b->stream>>>(b->dS, b->dmlist, b->nm);
+        count_launch();
         a = bargs(b, ROLE_KV0 + v, ROLE_H, ROLE_EVR, true);
         BCK(launch_apply(b->d, b->p, b->nq, P0, nullptr, nullptr, nullptr, b->desc.hess_precision,
-                         nullptr, k, b->stream, &a, b->nt_e));
+                         nullptr, KD, b->stream, &a, b->nt_e));
         if constexpr (std::is_same<R, double>::value) {
             if (D.hess_precision == TMOP_FP64)      // float-pair element vectors
                 b_assemble<df, double><<<b->nt_n, NCH, 0, b->stream>>>(
-                    b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z, 1, b->d, b->np, b->dS, k);
+                    b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z, 1, b->d, b->np, b->dS, KD);
             else
                 b_assemble<R, R><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EVR,
                                                                   ROLE_KV0 + Z, 1, b->d, b->np,
-                                                                  b->dS, k);
+                                                                  b->dS, KD);
         } else {
             b_assemble<R, R><<<b->nt_n, NCH, 0, b->stream>>>(b->dM, b->dtile_n, ROLE_EVR, ROLE_KV0 + Z,
-                                                              1, b->d, b->np, b->dS, k);
+                                                              1, b->d, b->np, b->dS, KD);
         }
-        b_lanczos_a<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R1, v, k);
-        b_fin_alpha<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, k);
-        b_lanczos_b<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R2, R1, k);
-        b_fin_beta<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, k, D.solver.minres_rtol,
+        b_lanczos_a<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R1, v, KD);
+        b_fin_alpha<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, KD);
+        b_lanczos_b<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, Z, R2, R1, KD);
+        b_fin_beta<<<b->nm, BT, 0, b->stream>>>(b->dM, b->dS, b->dmlist, KD, D.solver.minres_rtol,
                                                 D.solver.minres_fixed_its);
         b_minres_update<R><<<b->nt_v, BT, 0, b->stream>>>(b->dM, b->dtile_v, b->dS, v, W1, W2, W3, R1,
-                                                           k);
+                                                           KD);
         count_launch(6);
         BCK(cudaGetLastError());
+        return TMOP_OK;
+    };
+    auto rotate = [&] {
         const int oR1 = R1;
         R1 = R2;
         R2 = Z;
@@ -672,6 +710,61 @@ tmop_status setup_and_minres(tmop_batch *b)
         W1 = W2;
         W2 = W3;
         W3 = oW1;
+    };
+    // Blocks of 4 iterations as CUDA graphs (not on the legacy stream); the
+    // graph of a phase is captured once and replayed while the subset, its
+    // tables and the kernel variant stay the same.
+    const bool graphs = b->graphs && b->stream != nullptr;
+    const int variant = apply_variant(b->d, b->p, b->nq, D.hess_precision);
+    int k = 0;
+    while (k < max_it) {
+        if (graphs && max_it - k >= 4) {
+            tmop_batch::BGraph &g = b->bg[(k / 4) % 3];
+            if (!g.exec || g.subset != b->cur || g.ver != b->mesh_ver || g.te != b->dtile_e ||
+                g.tn != b->dtile_n || g.tv != b->dtile_v || g.variant != variant) {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+                cudaGraph_t graph = nullptr;
+                BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                const int64_t l0 = thread_launches();
+                tmop_status st = TMOP_OK;
+                for (int j = 0; j < 4 && st == TMOP_OK; ++j) {
+                    st = launch_iteration();
+                    rotate();
+                }
+                const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+                if (st != TMOP_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                BCK(ec);
+                const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ei != cudaSuccess) {
+                    g.exec = nullptr;
+                    BCK(ei);
+                }
+                g.subset = b->cur;
+                g.ver = b->mesh_ver;
+                g.te = b->dtile_e;
+                g.tn = b->dtile_n;
+                g.tv = b->dtile_v;
+                g.variant = variant;
+                g.nodes = (int)(thread_launches() - l0);
+                uncount_launches(g.nodes);                    // counted at each graph launch
+            } else {
+                for (int j = 0; j < 4; ++j) rotate();
+            }
+            BCK(cudaGraphLaunch(g.exec, b->stream));
+            count_launch(g.nodes);
+            ++b->graph_launches;
+            k += 4;
+        } else {
+            tmop_status st = launch_iteration();
+            if (st != TMOP_OK) return st;
+            rotate();
+            ++k;
+        }
         if (!D.solver.minres_fixed_its && k % 4 == 0 && k < max_it) {
             tmop_status st = read_states(b);
             if (st != TMOP_OK) return st;
@@ -866,6 +959,8 @@ tmop_status tmop_batch_add(tmop_batch *b, int64_t num_elems, int64_t num_nodes,
     b->hM[slot] = M;
     b->hS[slot] = S0;
     b->used[slot] = 1;
+    b->cur_valid = false;
+    ++b->mesh_ver;
     b->fault[slot] = TMOP_FAULT_NONE;
     *slot_out = slot;
     return TMOP_OK;
@@ -881,6 +976,8 @@ tmop_status tmop_batch_remove(tmop_batch *b, int slot)
     b->slab[slot] = nullptr;
     b->slab_bytes[slot] = 0;
     b->used[slot] = 0;
+    b->cur_valid = false;
+    ++b->mesh_ver;
     return TMOP_OK;
 }
 
@@ -944,6 +1041,15 @@ tmop_status tmop_batch_step(tmop_batch *b, int *n_active)
     return TMOP_OK;
 }
 
+tmop_status tmop_batch_set_graphs(tmop_batch *b, int on)
+{
+    if (!b) return bfail(TMOP_ERR_ARG, "NULL batch");
+    b->graphs = on != 0;
+    return TMOP_OK;
+}
+
+int64_t tmop_batch_graph_launches(const tmop_batch *b) { return b ? b->graph_launches : 0; }
+
 tmop_status tmop_batch_inject_fault(tmop_batch *b, int slot, int fault)
 {
     if (!b || slot < 0 || slot >= b->desc.max_meshes || !b->used[slot] ||
@@ -984,6 +1090,8 @@ void tmop_batch_destroy(tmop_batch *b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->bg)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (void *p : b->slab)
         if (p) cudaFree(p);
     cudaFree(b->tab);

@@ -59,6 +59,14 @@ void count_launch(int n)
     g_launches.fetch_add(n, std::memory_order_relaxed);
     t_launches += n;
 }
+
+int64_t thread_launches() { return t_launches; }
+
+void uncount_launches(int n)
+{
+    g_launches.fetch_sub(n, std::memory_order_relaxed);
+    t_launches -= n;
+}
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 }  // namespace tmop
 
@@ -615,8 +623,7 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
                 g.variant = variant;
                 g.lim = c->lim2 > 0.0;
                 g.nodes = (int)(t_launches - l0);
-                g_launches.fetch_sub(g.nodes, std::memory_order_relaxed);   // counted at launch
-                t_launches = l0;
+                uncount_launches(g.nodes);                    // counted at each graph launch
             } else {
                 for (int j = 0; j < 4; ++j) rotate();
             }

@@ -181,6 +181,10 @@ cudaError_t launch_min_accum(const double *part, int64_t nb, double *acc, int re
 
 // Global launch counter (instrumentation).
 void count_launch(int n = 1);
+// This thread's launch count, and the removal of n counted launches (the
+// launches recorded by a graph capture are counted when the graph runs).
+int64_t thread_launches();
+void uncount_launches(int n);
 
 // Text returned by tmop_last_error() on the calling thread.
 void set_last_error(const std::string &msg);

@@ -24,11 +24,11 @@ from .batch import TmopBatch, step_all
 class Server:
     def __init__(self, mem_budget_bytes: int, precision: str = "fp64", newton_rtol: float = 1e-6,
                  newton_max_it: int = 50, minres_rtol: float = 1e-8, minres_max_it: int = 50,
-                 max_meshes_per_group: int = 512, stream=None):
+                 max_meshes_per_group: int = 512, stream=None, graphs: bool = True):
         self.budget = int(mem_budget_bytes)
         self.kw = dict(precision=precision, newton_rtol=newton_rtol, newton_max_it=newton_max_it,
                        minres_rtol=minres_rtol, minres_max_it=minres_max_it,
-                       max_meshes=max_meshes_per_group, stream=stream)
+                       max_meshes=max_meshes_per_group, stream=stream, graphs=graphs)
         self.groups: dict = {}
         self.used = 0
         self.pool = ThreadPoolExecutor(max_workers=16)

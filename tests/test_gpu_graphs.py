@@ -67,3 +67,35 @@ def test_graphs_not_used_on_the_legacy_stream():
     assert gm.newton_step(x)["status"] == capi.OK
     assert capi.tmop_graph_launches(gm.ctx) == 0
     gm.close()
+
+
+def _batch_run(graphs, precision, join_leave):
+    from paper_2205_12721_b300 import meshgen as mg
+    from paper_2205_12721_b300.batch import TmopBatch
+    meshes = [mg.perturb_smooth(mg.structured(3, 2, s), seed=80 + i, amp_smooth=0.03, amp_noise=0.015)
+              for i, s in enumerate([(4, 3, 3), (3, 3, 2), (5, 4, 3), (2, 3, 2)])]
+    b = TmopBatch(3, 2, 302, precision=precision, max_meshes=8, minres_rtol=1e-8, minres_max_it=50,
+                  graphs=graphs)
+    slots = [b.add_structured(m) for m in meshes[:3]]
+    states = []
+    for step in range(4):
+        if join_leave and step == 1:
+            slots.append(b.add_structured(meshes[3]))
+        if join_leave and step == 2:
+            b.remove(slots.pop(1))
+        b.step()
+        states.append([(b.state(s)["minres_its"], b.state(s)["energy"]) for s in slots])
+    xs = [b.positions(s).cpu().numpy() for s in slots]
+    ng = capi.tmop_batch_graph_launches(b.handle)
+    b.close()
+    return xs, states, ng
+
+
+@pytest.mark.parametrize("precision,join_leave", [("fp64", False), ("fp64", True), ("fp32", True)])
+def test_batch_graphs_same_trajectory(precision, join_leave):
+    xg, sg, ng = _batch_run(True, precision, join_leave)
+    xd, sd, nd = _batch_run(False, precision, join_leave)
+    assert ng > 0 and nd == 0
+    assert sg == sd
+    for a, b in zip(xg, xd):
+        assert np.array_equal(a, b)
