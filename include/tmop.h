@@ -393,9 +393,11 @@ tmop_status tmop_profile_enable(tmop_ctx *ctx, int on);
  * one graph per phase of the work-vector rotation is captured on first use
  * and replayed while its parameters (output vector, tolerance, kernel
  * variant, limiting term) stay the same.  Graphs are not used while
- * profiling is enabled or when the context's stream is the legacy default
- * stream.  Results are the same either way (the same kernels in the same
- * order). */
+ * profiling is enabled.  When the context's stream is the legacy default
+ * stream (which cannot be captured), the MINRES solve runs on a stream the
+ * context creates, ordered after the work queued before the call and before
+ * the work queued after it (events).  Results are the same either way (the
+ * same kernels in the same order). */
 tmop_status tmop_set_graphs(tmop_ctx *ctx, int on);
 /* Number of MINRES graph launches of this context so far (diagnostics). */
 int64_t tmop_graph_launches(const tmop_ctx *ctx);

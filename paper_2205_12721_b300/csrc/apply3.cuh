@@ -139,6 +139,7 @@ __device__ __forceinline__ void apply3_body(ElemParams P, const RV *__restrict__
     // ---- pointwise: Y = H : dA with the symmetric-packed stored data
     if (qq) {
         const RC *He = H + e * (int64_t)C::HST;
+        const RC *Hc = He + (ty * NQ + tx);              // plain layout: the thread's column
 #pragma unroll
         for (int q3 = 0; q3 < NQ; ++q3) {
             RC y[9];
@@ -148,7 +149,8 @@ __device__ __forceinline__ void apply3_body(ElemParams P, const RV *__restrict__
             for (int r = 0; r < 9; ++r)
 #pragma unroll
                 for (int s = r; s < 9; ++s) {
-                    const RC h = He[C::hoff(pidx<9>(r, s), q3 * NQ * NQ + ty * NQ + tx)];
+                    const RC h = C::PAIRS ? He[C::hoff(pidx<9>(r, s), q3 * NQ * NQ + ty * NQ + tx)]
+                                          : Hc[pidx<9>(r, s) * NQD + q3 * NQ * NQ];
                     acc_add(y[r], h * col[s][q3]);
                     if (s != r) acc_add(y[s], h * col[r][q3]);
                 }
@@ -353,6 +355,7 @@ k_apply3s(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
 #pragma unroll
             for (int i3 = 0; i3 < NI; ++i3) z[r][i3] = 0;
         const RC *He = H + e * (int64_t)C::HST;
+        const RC *Hc = He + col;                         // plain layout: the thread's column
         // FP32 data at p = 4: three points per iteration let the stored-data loads
         // of the next points overlap (no spills; 24^3 Kershaw p = 4 0.578 -> 0.537 ms
         // per action, no gain at p <= 3); double-float would spill
@@ -382,7 +385,8 @@ k_apply3s(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
             for (int r = 0; r < 9; ++r)
 #pragma unroll
                 for (int s = r; s < 9; ++s) {
-                    const RC h = He[C::hoff(pidx<9>(r, s), q3 * NQ * NQ + col)];
+                    const RC h = C::PAIRS ? He[C::hoff(pidx<9>(r, s), q3 * NQ * NQ + col)]
+                                          : Hc[pidx<9>(r, s) * NQD + q3 * NQ * NQ];
                     acc_add(y[r], h * d[s]);
                     if (s != r) acc_add(y[s], h * d[r]);
                 }

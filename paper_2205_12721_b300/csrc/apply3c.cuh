@@ -369,34 +369,53 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
 
     // ---- pointwise: Y = H : dA with the symmetric-packed stored data; the
     // packed entries k = 0..NS-1 of a point in order, row 0 starting every sum
-    static_assert(NS == 45, "3D packed data");
+    static_assert(NS == 45 && C::PAIRS, "3D packed data in entry-pair planes");
     const RC *He = H + e * (int64_t)C::HST;
     const int pt = ty * NQ + tx;                            // the thread's point of a q3 plane
-    // the terms of packed entry KK (row r <= column s, value h)
-    auto term = [](auto KK, const RC &h, const RC *d, RC *y) {
+    // the terms of packed entry KK (row r <= column s, value h); FP32 / FP64
+    // multiply-adds as explicit FMAs, so that every variant rounds alike
+    auto mac = [](RC &acc, const RC &a, const RC &b) {
+        if constexpr (std::is_same<RC, df>::value) acc_add(acc, a * b);
+        else acc = fma(a, b, acc);
+    };
+    auto term = [&](auto KK, const RC &h, const RC *d, RC *y) {
         constexpr int kk = decltype(KK)::value;
         constexpr int r = prow9(kk), sc = pcol9(kk);
         if constexpr (r == 0) {
             y[sc] = mul1(h, d[0]);
-            if constexpr (sc > 0) acc_add(y[0], h * d[sc]);
+            if constexpr (sc > 0) mac(y[0], h, d[sc]);
         } else {
-            acc_add(y[sc], h * d[r]);
-            if constexpr (sc != r) acc_add(y[r], h * d[sc]);
+            mac(y[sc], h, d[r]);
+            if constexpr (sc != r) mac(y[r], h, d[sc]);
         }
     };
+    // the stored values of point q: entry pair planes from He + 2 q, the last
+    // entry's plane from He + q (compile-time offsets from the two bases)
+    constexpr int LAST = 2 * C::NPR * NQD;
+    static_assert(C::hoff(3, 5) == 2 * 5 + 2 * NQD + 1 && C::hoff(NS - 1, 5) == LAST + 5,
+                  "the point loop's offsets are those of the stored layout");
     // L2 prefetch of the stored values of point q (one line per entry pair)
     auto prefetch_point = [&](int q) {
+        const RC *Hp = He + 2 * q;
 #pragma unroll
-        for (int g = 0; g <= C::NPR; ++g)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(He + C::hoff(2 * g, q)));
+        for (int g = 0; g < C::NPR; ++g)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Hp + 2 * g * NQD));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(He + q + LAST));
+    };
+    // value of packed entry kk (compile time) at point q
+    auto hval = [&](auto KK, int q) -> RC {
+        constexpr int kk = decltype(KK)::value;
+        if constexpr (kk < 2 * C::NPR)
+            return ld_stream(He + 2 * q + (2 * (kk >> 1) * NQD + (kk & 1)));
+        else
+            return ld_stream(He + q + LAST);
     };
     if (PIPE && SC && valid) {
         constexpr int CH = 9, NCH = 5;                  // 45 = 5 chunks of 9 per point
         constexpr int NJ = NQ * NCH;
         constexpr int UJ = (NQ % 2 == 0) ? 2 * NCH : NJ;   // chunks per unrolled body
         RC hb0[CH], hb1[CH];                            // the two chunk buffers
-#pragma unroll
-        for (int t2 = 0; t2 < CH; ++t2) hb0[t2] = ld_stream(He + C::hoff(t2, pt));
+        static_for<CH>([&](auto T2) { hb0[decltype(T2)::value] = hval(T2, pt); });
 #pragma unroll 1
         for (int j0 = 0; j0 < NJ; j0 += UJ) {
             RC d[9], y[9];
@@ -409,8 +428,10 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
                 const int q3 = j0 / NCH + jj / NCH;
                 if (j0 + jj + 1 < NJ) {                 // loads of the next chunk
                     const int qn = (j0 / NCH + (jj + 1) / NCH) * NQ * NQ + pt;
-#pragma unroll
-                    for (int t2 = 0; t2 < CH; ++t2) nxt[t2] = ld_stream(He + C::hoff(c1 * CH + t2, qn));
+                    static_for<CH>([&](auto T2) {
+                        constexpr int t2 = decltype(T2)::value;
+                        nxt[t2] = hval(std::integral_constant<int, c1 * CH + t2>{}, qn);
+                    });
                     if (PFN && c == 0 && q3 + 1 < NQ) prefetch_point((q3 + 1) * NQ * NQ + pt);
                 }
                 if constexpr (c == 0) {
@@ -436,14 +457,15 @@ k_apply3c(ElemParams P, const RV *__restrict__ v, const RC *__restrict__ H, RV *
             RC d[9], y[9];
 #pragma unroll
             for (int r = 0; r < 9; ++r) d[r] = COLW(r, q3);
+            const RC *Hp = He + 2 * q;
             static_for<C::NPR>([&](auto G) {            // entries 2g, 2g+1: one pair load
                 constexpr int g = decltype(G)::value;
                 RC h0, h1;
-                ld_stream2(He + C::hoff(2 * g, q), h0, h1);
+                ld_stream2(Hp + 2 * g * NQD, h0, h1);
                 term(std::integral_constant<int, 2 * g>{}, h0, d, y);
                 term(std::integral_constant<int, 2 * g + 1>{}, h1, d, y);
             });
-            term(std::integral_constant<int, NS - 1>{}, ld_stream(He + C::hoff(NS - 1, q)), d, y);
+            term(std::integral_constant<int, NS - 1>{}, ld_stream(He + q + LAST), d, y);
 #pragma unroll
             for (int r = 0; r < 9; ++r) COLW(r, q3) = y[r];
         }

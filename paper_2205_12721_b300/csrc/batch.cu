@@ -533,7 +533,7 @@ SlabPlan plan_slab(const tmop_batch *b, int64_t E, int64_t Nx, bool has_fixed)
     s.off[ROLE_XT] = take(8 * ndof);
     s.off[ROLE_G] = take(8 * ndof);
     s.off[ROLE_DX] = take(8 * ndof);
-    s.off[ROLE_H] = take((int64_t)b->rsz * E * h_stride(b->ns, b->nqd) + 256);
+    s.off[ROLE_H] = take((int64_t)b->rsz * E * h_stride(b->d, b->nq, b->ns, b->nqd) + 256);
     s.off[ROLE_EV64] = take(8 * b->d * ENP);
     s.off[ROLE_EVR] = (b->vprec == TMOP_FP32) ? take(4 * b->d * ENP) : s.off[ROLE_EV64];
     s.off[ROLE_DIAG] = take((int64_t)b->rsz * ndof);

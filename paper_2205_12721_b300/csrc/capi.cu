@@ -104,6 +104,10 @@ struct tmop_ctx {
     // rotation (the 4-buffer rotation returns to its start every 4 iterations)
     bool graphs = true;
     int64_t graph_launches = 0;
+    // the context's own stream for graph-captured solves when its stream is the
+    // legacy default stream (which cannot be captured), and the handoff event
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev = nullptr;
     struct MinresGraph {
         cudaGraphExec_t exec = nullptr;
         const double *dx = nullptr;
@@ -521,9 +525,10 @@ tmop_status diag_async(tmop_ctx *c, void *diag)
     return TMOP_OK;
 }
 
-// Jacobi-preconditioned MINRES for H dx = b (b FP64, zero on fixed DOFs).
-tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int max_it,
-                   int fixed_its, int *iters, double *resid, int *breakdown)
+// Jacobi-preconditioned MINRES for H dx = b (b FP64, zero on fixed DOFs), on
+// the context's stream.
+tmop_status minres_on(tmop_ctx *c, const double *b, double *dx, double rtol, int max_it,
+                      int fixed_its, int *iters, double *resid, int *breakdown)
 {
     const int64_t n = c->ndof;
     const int pr = c->vprec;
@@ -650,6 +655,29 @@ tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int ma
     return TMOP_OK;
 }
 
+// MINRES; with graphs on and the legacy default stream as the context's
+// stream, the solve runs on the context's own non-blocking stream, after the
+// work already queued on the legacy stream and before the work queued later
+// (event handoff both ways).
+tmop_status minres(tmop_ctx *c, const double *b, double *dx, double rtol, int max_it,
+                   int fixed_its, int *iters, double *resid, int *breakdown)
+{
+    if (!(c->graphs && !c->prof && c->stream == nullptr))
+        return minres_on(c, b, dx, rtol, max_it, fixed_its, iters, resid, breakdown);
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(c->gev, nullptr));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev, 0));
+    c->stream = c->gstream;
+    const tmop_status st = minres_on(c, b, dx, rtol, max_it, fixed_its, iters, resid, breakdown);
+    c->stream = nullptr;
+    CK(cudaEventRecord(c->gev, c->gstream));
+    CK(cudaStreamWaitEvent(nullptr, c->gev, 0));
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -680,6 +708,11 @@ void tmop_destroy(tmop_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto &g : ctx->mg)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->gstream) {
+        cudaStreamSynchronize(ctx->gstream);
+        cudaStreamDestroy(ctx->gstream);
+    }
+    if (ctx->gev) cudaEventDestroy(ctx->gev);
     for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     for (void *q : ctx->allocs) cudaFree(q);
@@ -808,7 +841,7 @@ tmop_status tmop_setup(const tmop_desc *desc, const int32_t *elem_to_node, const
     SCK(cudaMemcpyAsync(c->tabf, tabf.data(), sizeof(float) * tabn, cudaMemcpyHostToDevice, c->stream));
     // stored Hessian data, element vectors, reductions, work vectors
     // padded to a 256-byte multiple: the action kernels prefetch whole 16-byte lines
-    STRY(c->alloc_raw(&c->H, ((c->rsz * (size_t)c->E * h_stride(c->ns, c->nqd) + 255) / 256) * 256 + 256));
+    STRY(c->alloc_raw(&c->H, ((c->rsz * (size_t)c->E * h_stride(c->d, c->nq, c->ns, c->nqd) + 255) / 256) * 256 + 256));
     STRY(c->alloc(&c->ev64, (size_t)c->d * c->ENP));
     if (c->vprec == TMOP_FP32) STRY(c->alloc_raw(&c->evR, 4 * (size_t)c->d * c->ENP));
     else c->evR = c->ev64;

@@ -441,6 +441,41 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
 }
 
 // ---------------------------------------------------------------- Hessian setup
+// Two consecutive stored values in one store (an entry pair of the PAIRS
+// layout; p aligned to their combined size).
+__device__ __forceinline__ void st_pair(df *p, const df &a, const df &b)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a.h, a.l, b.h, b.l);
+}
+__device__ __forceinline__ void st_pair(float *p, float a, float b)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(double *p, double a, double b)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+
+// The stores of one point's packed entries, made in increasing entry order:
+// with the PAIRS layout an even entry is held until its odd partner and the
+// two are stored together.
+template <class C, class RH>
+struct PointStore {
+    RH *He;
+    int q;
+    RH pend;
+    __device__ __forceinline__ void put(int k, const RH &v)
+    {
+        if constexpr (!C::PAIRS) {
+            He[C::hoff(k, q)] = v;
+        } else {
+            if ((C::NS & 1) && k == C::NS - 1) He[C::hoff(k, q)] = v;
+            else if ((k & 1) == 0) pend = v;
+            else st_pair(He + C::hoff(k - 1, q), pend, v);
+        }
+    }
+};
+
 // HAS_I2 = false: metrics of (I1, tau) only (mu_2, mu_303, mu_55, mu_303 + mu_55,
 // and the 2D mu_7, mu_9),
 // whose d2mu/dT2 is u (x) g1 + w (x) cof T + 2 f1 Id + f_tau d2tau with
@@ -506,6 +541,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                 ft = from_db<df>(sc * v.ft);
             }
             df u[C::DD], w[C::DD];
+            PointStore<C, RH> ps{He, q, RH()};
 #pragma unroll
             for (int r = 0; r < C::DD; ++r) {
                 df x(0.0f, 0.0f), y(0.0f, 0.0f);
@@ -538,7 +574,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                             acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
                         }
                     }
-                    He[C::hoff(pidx<C::DD>(r, s), q)] = store_dw<RH>(norm(k));
+                    ps.put(pidx<C::DD>(r, s), store_dw<RH>(norm(k)));
                 }
             return;
         }
@@ -549,6 +585,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
             // u = f11 g1 + f1t Cf + f12 g2 + 2 f2 T, w = f1t g1 + ftt Cf + f2t g2,
             // z = f12 g1 + f2t Cf (f22 = 0), g1 = 2T: d2I2 = 4 T (x) T + 2 I1 Id - ...
             df Td[9], Cd[9], g2w[9], TtTw[9], TTtw[9], I1w;
+            PointStore<C, RH> ps{He, q, RH()};
             double I1, tau;
             point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
             if (!(tau > 0.0) || !(ws > 0.0)) {
@@ -600,7 +637,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                     if (a == cc) acc_add(k, m2 * TtTw[e * 3 + b]);
                     acc_add(k, m2 * to_df(Td[a * 3 + e] * Td[cc * 3 + b]));
                     if (b == e) acc_add(k, m2 * TTtw[a * 3 + cc]);
-                    He[C::hoff(pidx<9>(r, s), q)] = store_dw<RH>(norm(k));
+                    ps.put(pidx<9>(r, s), store_dw<RH>(norm(k)));
                 }
             return;
         }
@@ -617,14 +654,15 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
         Inv v;
         metric_scalars<C::D>(P.metric, I1, tau, I2, v);
         const double sc = cq * iws * iws;
+        PointStore<C, RH> ps{He, q, RH()};
         if constexpr (HAS_I2) {
             if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
 #pragma unroll
             for (int r = 0; r < C::DD; ++r)
 #pragma unroll
                 for (int s = r; s < C::DD; ++s)
-                    He[C::hoff(pidx<C::DD>(r, s), q)] =
-                        from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v));
+                    ps.put(pidx<C::DD>(r, s),
+                           from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v)));
         } else {
             double u[C::DD], w[C::DD];
 #pragma unroll
@@ -644,7 +682,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
                         if (C::D == 2) k += ft * ((a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0));
                         else k += ft * eps3(a, cc) * eps3(b, e) * T[(3 - a - cc) * 3 + (3 - b - e)];
                     }
-                    He[C::hoff(pidx<C::DD>(r, s), q)] = from_db<RH>(k);
+                    ps.put(pidx<C::DD>(r, s), from_db<RH>(k));
                 }
         }
     });

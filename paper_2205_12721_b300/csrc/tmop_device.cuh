@@ -47,15 +47,21 @@ struct Cfg {
     static constexpr int NQD = D == 3 ? NQ * NQ * NQ : NQ * NQ;
     static constexpr int DD = D * D;
     static constexpr int NS = DD * (DD + 1) / 2;            // packed symmetric H
-    // Stored d2mu/dT2 of one element (entries s of the packed upper triangle
-    // at the NQD points): NS/2 planes of entry pairs, entries 2g and 2g+1 of a
-    // point side by side, then for odd NS the plane of the last entry; element
-    // blocks of HST values, a multiple of 4, so that pair loads are aligned.
+    // Stored d2mu/dT2 of one element: entries s of the packed upper triangle
+    // at the NQD points, in element blocks of HST values (PAIRS: rounded up to
+    // a multiple of 4 for aligned pair loads).
+    // PAIRS (3D, an element's n_q x n_q columns in one warp: the collocated
+    // action kernels, which load two entries at once): NS/2 planes of entry
+    // pairs, entries 2g and 2g+1 of a point side by side, then for odd NS the
+    // plane of the last entry.  Otherwise one plane per entry, [s][q], for the
+    // kernels that read one entry at a time across consecutive points.
+    static constexpr bool PAIRS = D == 3 && NQ * NQ <= 32;
     static constexpr int NPR = NS / 2;
-    static constexpr int HST = (NS * NQD + 3) & ~3;
+    static constexpr int HST = PAIRS ? (NS * NQD + 3) & ~3 : NS * NQD;
     static __host__ __device__ constexpr int hoff(int s, int q)
     {
-        return s < 2 * NPR ? ((s >> 1) * NQD + q) * 2 + (s & 1) : 2 * NPR * NQD + q;
+        return !PAIRS ? s * NQD + q
+                      : (s < 2 * NPR ? ((s >> 1) * NQD + q) * 2 + (s & 1) : 2 * NPR * NQD + q);
     }
     static constexpr int TPE = MX * MX;                      // threads per element
     // elements per CTA: ~128 threads in 3D, ~256 in 2D.  In 3D, when an

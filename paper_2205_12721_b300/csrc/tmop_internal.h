@@ -29,9 +29,13 @@ enum { ARITH_DW = 0, ARITH_NATIVE = 1 };
 // Element-vector format of the double-float Hessian action (TMOP_FP64): float
 // pairs in 8-byte slots (dfloat.cuh, EvPair), an ev_prec of launch_assemble.
 enum { EV_DF_PAIR = 16 };
-// Values of stored d2mu/dT2 per element (Cfg::HST: ns entries at nqd points,
-// rounded up to a multiple of 4 for aligned entry-pair loads).
-inline int64_t h_stride(int ns, int nqd) { return ((int64_t)ns * nqd + 3) & ~(int64_t)3; }
+// Values of stored d2mu/dT2 per element (Cfg::HST: ns entries at nqd points;
+// in 3D with nq^2 <= 32, the entry-pair layout, rounded up to a multiple of 4).
+inline int64_t h_stride(int d, int nq, int ns, int nqd)
+{
+    const int64_t n = (int64_t)ns * nqd;
+    return (d == 3 && nq * nq <= 32) ? (n + 3) & ~(int64_t)3 : n;
+}
 // Element-vector format written by the Hessian action of a precision.
 inline int action_ev_format(int hess_precision)
 {

@@ -60,13 +60,25 @@ def test_graphs_same_trajectory(d, p, metric, shape, precision, opts, limit, swi
     assert lg == ld                  # graph nodes counted as launches
 
 
-def test_graphs_not_used_on_the_legacy_stream():
+def test_graphs_on_the_legacy_stream():
+    """A context on the legacy default stream runs its graph-captured MINRES
+    on a stream of its own, ordered by events before and after: the same
+    trajectory as with separate launches, and work queued after the step on
+    the legacy stream sees the new positions."""
     m = make_case(3, 2, (3, 3, 2), seed=5)
-    gm = TmopMesh(m.dim, m.order, m.map, m.num_nodes, 302, fixed=m.fixed)
-    x = dev(m.x)
-    assert gm.newton_step(x)["status"] == capi.OK
-    assert capi.tmop_graph_launches(gm.ctx) == 0
-    gm.close()
+    out = []
+    for graphs in (True, False):
+        gm = TmopMesh(m.dim, m.order, m.map, m.num_nodes, 302, fixed=m.fixed)
+        capi.tmop_set_graphs(gm.ctx, graphs)
+        x = dev(m.x)
+        reps = [gm.newton_step(x) for _ in range(3)]
+        y = x * 2.0
+        out.append((host(x), host(y), [r["energy"] for r in reps], capi.tmop_graph_launches(gm.ctx)))
+        gm.close()
+    assert out[0][3] > 0 and out[1][3] == 0
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][1], 2.0 * out[0][0])
+    assert out[0][2] == out[1][2]
 
 
 def _batch_run(graphs, precision, join_leave):
