@@ -2,8 +2,43 @@
 // (dim, order, nq1d) and both contraction arithmetics (FP64 units or
 // double-float on the FP32 units).
 #include "elem_launch.cuh"
+#include "grad3c.cuh"
 
 namespace tmop {
+
+// Tables of the warp-synchronous gradient for one (NI, NQ), built once per process.
+template <int NI, int NQ>
+static const GradTab<df, NI, NQ> &gradtab()
+{
+    static const GradTab<df, NI, NQ> T = [] {
+        GradTab<df, NI, NQ> t;
+        double B[NQ * NI], G[NQ * NI], w[NQ];
+        host_basis_tables(NI, NQ, B, G, w);
+        for (int i = 0; i < NQ * NI; ++i) t.B[i] = df(B[i]);
+        for (int i = 0; i < NQ * NI; ++i) t.G[i] = df(G[i]);
+        for (int i = 0; i < NQ; ++i) t.w[i] = df(w[i]);
+        return t;
+    }();
+    return T;
+}
+
+// The warp-synchronous gradient (3D, an element's n_q x n_q columns in one
+// warp, double-float); the register budget of 16 resident warps (12 at n_q = 5,
+// whose point algebra would spill at 16).
+template <class C>
+static cudaError_t run_grad3c(const ElemParams &P, const double *x, double *ev, double *part,
+                              cudaStream_t s, const BatchArgs &B, int64_t ntiles)
+{
+    const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
+    if (nb == 0) return cudaSuccess;
+    constexpr size_t bytes = Grad3cShape<C>::bytes;
+    auto kern = k_grad3c<C, (C::NQ >= 5 ? 3 : 4)>;
+    cudaError_t e = prepare(kern, bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nb, C::NT, bytes, s>>>(P, x, ev, part, B, gradtab<C::NI, C::NQ>());
+    count_launch();
+    return cudaGetLastError();
+}
 
 template <class C, class RS>
 static cudaError_t run_energy(const ElemParams &P, const double *x, double *part, cudaStream_t s,
@@ -23,6 +58,9 @@ template <class C, class RS>
 static cudaError_t run_gradient(const ElemParams &P, const double *x, double *ev, double *part,
                                 cudaStream_t s, const BatchArgs &B, int64_t ntiles)
 {
+    if constexpr (C::D == 3 && C::NQ * C::NQ <= 32 && std::is_same<RS, df>::value) {
+        if (P.target != TGT_DISCRETE) return run_grad3c<C>(P, x, ev, part, s, B, ntiles);
+    }
     using L = Layout<C, RS>;
     const int64_t nb = B.tiles ? ntiles : grid_of<C>(P.E);
     if (nb == 0) return cudaSuccess;

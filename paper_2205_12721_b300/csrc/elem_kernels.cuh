@@ -302,6 +302,120 @@ k_energy(ElemParams P, const double *__restrict__ x, double *__restrict__ part, 
 // decision is per point and per call: a result depends only on x.
 constexpr double kMuFp64Below = 1e-6;
 
+// The gradient integrand at one point (and its energy, det A): reads the
+// Jacobian A_r at sA[r * ST + q] (r = 0..DD-1), writes c_q dmu/dT(T) W^-T into
+// the same slots (zero at an inverted point), adds c_q mu to esum (mu from FP64
+// invariants where |mu| < kMuFp64Below, when want_e) and det A to the minimum
+// emin.  ws: target scale (W = ws I), iws = 1/ws, wd = ws^D, cq = w_q wd.
+template <class C, int ST, class RS>
+__device__ __forceinline__ void gradient_point(const ElemParams &P, RS *sA, int q, double ws,
+                                               double iws, double wd, double cq, bool want_e,
+                                               double &esum, double &emin)
+{
+    const bool dw = std::is_same<RS, df>::value;
+    const bool use_i2 = metric_uses_I2(P.metric, C::D);
+    if constexpr (std::is_same<RS, df>::value) {
+        if (dw && !use_i2) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
+            df Td[C::DD], Cd[C::DD], I1w, tauw;
+            double I1, tau;
+            point_T_dw<C::D, ST>(sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau,
+                                     &I1w, &tauw);
+            emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+            if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                for (int r = 0; r < C::DD; ++r) sA[r * ST + q] = RS(0.0f, 0.0f);
+                return;
+            }
+            const double sc = cq * iws;
+            df a, b;
+            double mu_pt;
+            if (P.metric == MET_303 || P.metric == MET_303_55) {   // scalars in double-float too
+                InvW w;
+                mu_pt = to_db(metric303_dw(I1w, tauw, P.metric == MET_303_55, w));
+                const df scw = from_db<df>(sc);
+                a = dw_mul(scw, df(2.0f * w.f1.h, 2.0f * w.f1.l));
+                b = dw_mul(scw, w.ft);
+            } else {
+                Inv v;
+                mu_pt = metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+                a = from_db<df>(2.0 * v.f1 * sc);
+                b = from_db<df>(v.ft * sc);
+            }
+            if (want_e && fabs(mu_pt) < kMuFp64Below) {
+                double Tdb[C::DD];             // energy from FP64 invariants
+#pragma unroll
+                for (int r = 0; r < C::DD; ++r) Tdb[r] = to_db(Td[r]);
+                mu_pt = metric_mu_fp64<C::D>(P.metric, Tdb);
+            }
+            esum += cq * mu_pt;
+#pragma unroll
+            for (int r = 0; r < C::DD; ++r) {
+                df acc(0.0f, 0.0f);
+                acc_add(acc, a * Td[r]);
+                acc_add(acc, b * Cd[r]);
+                sA[r * ST + q] = norm(acc);
+            }
+            return;
+        }
+        if constexpr (C::D == 3) {
+            if (dw && use_i2) {   // I2 metrics: + f2 dI2/dT, dI2/dT = 2 (I1 T - T T^T T)
+                df Td[9], Cd[9], g2[9], TtT[9], TTt[9], I1w;
+                double I1, tau;
+                point_T_dw<3, ST>(sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
+                emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+                if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) sA[r * ST + q] = RS(0.0f, 0.0f);
+                    return;
+                }
+                const double I2 = i2_dw(Td, Cd, I1w, g2, TtT, TTt);
+                Inv v;
+                const double mu = metric_scalars<3>(P.metric, I1, tau, I2, v);
+                if (want_e && fabs(mu) < kMuFp64Below) {
+                    double Tdb[9];             // energy from FP64 invariants
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) Tdb[r] = to_db(Td[r]);
+                    esum += cq * metric_mu_fp64<3>(P.metric, Tdb);
+                } else {
+                    esum += cq * mu;
+                }
+                const double sc = cq * iws;
+                const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
+                const df c2 = from_db<df>(v.f2 * sc);
+#pragma unroll
+                for (int r = 0; r < 9; ++r) {
+                    df acc(0.0f, 0.0f);
+                    acc_add(acc, a * Td[r]);
+                    acc_add(acc, b * Cd[r]);
+                    acc_add(acc, c2 * g2[r]);
+                    sA[r * ST + q] = norm(acc);
+                }
+                return;
+            }
+        }
+    }
+    double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
+#pragma unroll
+    for (int r = 0; r < C::DD; ++r) T[r] = to_db(sA[r * ST + q]) * iws;
+    double I1, tau, I2;
+    invariants<C::D>(T, I1, tau, I2, Cf);
+    emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
+    if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points contribute 0
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) sA[r * ST + q] = RS(0.0);
+        return;
+    }
+    Inv v;
+    esum += cq * metric_scalars<C::D>(P.metric, I1, tau, I2, v);
+    if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
+    const double sc = cq * iws;
+#pragma unroll
+    for (int r = 0; r < C::DD; ++r) {
+        double pr = v.f1 * 2.0 * T[r] + v.ft * Cf[r];
+        if (C::D == 3 && v.f2 != 0.0) pr += v.f2 * g2[r];
+        sA[r * ST + q] = from_db<RS>(sc * pr);
+    }}
+
 template <class C, class RS>
 __global__ void __launch_bounds__(C::NT)
 k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, double *part,
@@ -321,8 +435,6 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
     forward_geometry<C, RS>(P, c, x);
 
     double esum = 0.0, emin = INFINITY;
-    const bool dw = std::is_same<RS, df>::value;
-    const bool use_i2 = metric_uses_I2(P.metric, C::D);
     for_my_points<C>(c.tx, c.ty, c.valid, [&](int q, int q3) {
         double ws = 1.0, iws = 1.0, wd = 1.0;            // identity target: W = I
         if (P.target != TGT_IDENTITY) {
@@ -333,107 +445,7 @@ k_gradient(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, 
             for (int k = 1; k < C::D; ++k) wd *= ws;
         }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
-        if constexpr (std::is_same<RS, df>::value) {
-            if (dw && !use_i2) {      // (I1, tau) metrics: P = 2 f1 T + f_tau cof T on the FP32 pipes
-                df Td[C::DD], Cd[C::DD], I1w, tauw;
-                double I1, tau;
-                point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau,
-                                         &I1w, &tauw);
-                emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
-                if (!(tau > 0.0) || !(ws > 0.0)) {
-#pragma unroll
-                    for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0f, 0.0f);
-                    return;
-                }
-                const double sc = cq * iws;
-                df a, b;
-                double mu_pt;
-                if (P.metric == MET_303 || P.metric == MET_303_55) {   // scalars in double-float too
-                    InvW w;
-                    mu_pt = to_db(metric303_dw(I1w, tauw, P.metric == MET_303_55, w));
-                    const df scw = from_db<df>(sc);
-                    a = dw_mul(scw, df(2.0f * w.f1.h, 2.0f * w.f1.l));
-                    b = dw_mul(scw, w.ft);
-                } else {
-                    Inv v;
-                    mu_pt = metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
-                    a = from_db<df>(2.0 * v.f1 * sc);
-                    b = from_db<df>(v.ft * sc);
-                }
-                if (part && fabs(mu_pt) < kMuFp64Below) {
-                    double Tdb[C::DD];             // energy from FP64 invariants
-#pragma unroll
-                    for (int r = 0; r < C::DD; ++r) Tdb[r] = to_db(Td[r]);
-                    mu_pt = metric_mu_fp64<C::D>(P.metric, Tdb);
-                }
-                esum += cq * mu_pt;
-#pragma unroll
-                for (int r = 0; r < C::DD; ++r) {
-                    df acc(0.0f, 0.0f);
-                    acc_add(acc, a * Td[r]);
-                    acc_add(acc, b * Cd[r]);
-                    c.sA[r * C::NQD + q] = norm(acc);
-                }
-                return;
-            }
-            if constexpr (C::D == 3) {
-                if (dw && use_i2) {   // I2 metrics: + f2 dI2/dT, dI2/dT = 2 (I1 T - T T^T T)
-                    df Td[9], Cd[9], g2[9], TtT[9], TTt[9], I1w;
-                    double I1, tau;
-                    point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
-                    emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
-                    if (!(tau > 0.0) || !(ws > 0.0)) {
-#pragma unroll
-                        for (int r = 0; r < 9; ++r) c.sA[r * C::NQD + q] = RS(0.0f, 0.0f);
-                        return;
-                    }
-                    const double I2 = i2_dw(Td, Cd, I1w, g2, TtT, TTt);
-                    Inv v;
-                    const double mu = metric_scalars<3>(P.metric, I1, tau, I2, v);
-                    if (part && fabs(mu) < kMuFp64Below) {
-                        double Tdb[9];             // energy from FP64 invariants
-#pragma unroll
-                        for (int r = 0; r < 9; ++r) Tdb[r] = to_db(Td[r]);
-                        esum += cq * metric_mu_fp64<3>(P.metric, Tdb);
-                    } else {
-                        esum += cq * mu;
-                    }
-                    const double sc = cq * iws;
-                    const df a = from_db<df>(2.0 * v.f1 * sc), b = from_db<df>(v.ft * sc);
-                    const df c2 = from_db<df>(v.f2 * sc);
-#pragma unroll
-                    for (int r = 0; r < 9; ++r) {
-                        df acc(0.0f, 0.0f);
-                        acc_add(acc, a * Td[r]);
-                        acc_add(acc, b * Cd[r]);
-                        acc_add(acc, c2 * g2[r]);
-                        c.sA[r * C::NQD + q] = norm(acc);
-                    }
-                    return;
-                }
-            }
-        }
-        double T[C::DD], Cf[C::DD], g2[C::DD], TtT[9], TTt[9];
-#pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
-        double I1, tau, I2;
-        invariants<C::D>(T, I1, tau, I2, Cf);
-        emin = fmin(emin, ws > 0.0 ? tau * wd : -INFINITY);
-        if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points contribute 0
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r) c.sA[r * C::NQD + q] = RS(0.0);
-            return;
-        }
-        Inv v;
-        esum += cq * metric_scalars<C::D>(P.metric, I1, tau, I2, v);
-        if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
-        const double sc = cq * iws;
-#pragma unroll
-        for (int r = 0; r < C::DD; ++r) {
-            double pr = v.f1 * 2.0 * T[r] + v.ft * Cf[r];
-            if (C::D == 3 && v.f2 != 0.0) pr += v.f2 * g2[r];
-            c.sA[r * C::NQD + q] = from_db<RS>(sc * pr);
-        }
+        gradient_point<C, C::NQD, RS>(P, c.sA, q, ws, iws, wd, cq, part != nullptr, esum, emin);
     });
     if (part) cta_energy_reduce<C>(esum, emin, part, tile);   // part is uniform per launch
     __syncthreads();

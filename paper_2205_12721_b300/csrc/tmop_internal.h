@@ -39,8 +39,8 @@ inline int64_t h_stride(int d, int nq, int ns, int nqd)
 // Element-vector format written by the Hessian action of a precision.
 inline int action_ev_format(int hess_precision)
 {
-    return hess_precision == TMOP_FP64 ? EV_DF_PAIR
-                                       : (hess_precision == TMOP_FP32 ? TMOP_FP32 : TMOP_FP64);
+    return hess_precision == TMOP_FP64 ? (int)EV_DF_PAIR
+                                       : (hess_precision == TMOP_FP32 ? (int)TMOP_FP32 : (int)TMOP_FP64);
 }
 
 // Element-kernel launchers (one translation unit each).  Return the launch
