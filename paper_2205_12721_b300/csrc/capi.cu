@@ -534,11 +534,13 @@ tmop_status minres_on(tmop_ctx *c, const double *b, double *dx, double rtol, int
     const int pr = c->vprec;
     const size_t vb = c->rsz * (size_t)n;
     const int nb = reduce_blocks(n);
-    // FP32 vectors: the assembly fused with the first Lanczos update (one
-    // pass less over z; 0.43 -> 0.40 ms per iteration at 48^3 Q3).  FP64
-    // vectors: separate kernels, the fused grid-stride gather measured no
-    // faster than the one-node-per-thread assembly followed by the update.
-    const bool fuse = pr == TMOP_FP32;
+    // The assembly fused with the first Lanczos update (one pass less over z)
+    // for FP32 vectors (0.43 -> 0.40 ms per iteration at 48^3 Q3) and for the
+    // float-pair element vectors of the double-float action (Newton step
+    // 28.87 -> 28.72 ms); with FP64 element vectors (native FP64) the fused
+    // grid-stride gather measured no faster than the one-node-per-thread
+    // assembly followed by the update.
+    const bool fuse = pr == TMOP_FP32 || action_ev_format(c->prec) == EV_DF_PAIR;
     void *v = c->kv[0], *R1 = c->kv[1], *R2 = c->kv[2], *Z = c->kv[3];
     void *W1 = c->kv[4], *W2 = c->kv[5], *W3 = c->kv[6];
     CK(cudaMemsetAsync(dx, 0, sizeof(double) * n, c->stream));
@@ -559,8 +561,9 @@ tmop_status minres_on(tmop_ctx *c, const double *b, double *dx, double rtol, int
         if (fuse) {
             TRY(timed(c, TMOP_K_ASSEMBLE, "assemble + lanczos", [&] {
                 return launch_assemble_lanczos_a(c->evR, c->csr_ptr, c->csr_idx, c->fixed, c->Nx,
-                                                 c->d, c->ENP, Z, R1, v, c->st, pr, KD, c->part, nb,
-                                                 c->stream);
+                                                 c->d, c->ENP, Z, R1, v, c->st,
+                                                 pr == TMOP_FP32 ? pr : action_ev_format(c->prec), KD,
+                                                 c->part, nb, c->stream);
             }));
         } else {
             TRY(timed(c, TMOP_K_ASSEMBLE, "assemble", [&] {

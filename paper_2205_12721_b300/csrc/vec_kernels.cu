@@ -713,6 +713,10 @@ cudaError_t launch_assemble_lanczos_a(const void *ev, const int32_t *ptr, const 
         k_assemble_lanczos_a<float, float><<<nb, VT, 0, s>>>(
             (const float *)ev, ptr, idx, fixed, Nx, D, ENP, (float *)y, (const float *)r1,
             (const float *)v, st, k, part);
+    else if (prec == EV_DF_PAIR)                      // float-pair entries, FP64 vectors
+        k_assemble_lanczos_a<df, double><<<nb, VT, 0, s>>>(
+            (const df *)ev, ptr, idx, fixed, Nx, D, ENP, (double *)y, (const double *)r1,
+            (const double *)v, st, k, part);
     else
         k_assemble_lanczos_a<double, double><<<nb, VT, 0, s>>>(
             (const double *)ev, ptr, idx, fixed, Nx, D, ENP, (double *)y, (const double *)r1,
