@@ -492,6 +492,194 @@ struct PointStore {
 // and the 2D mu_7, mu_9),
 // whose d2mu/dT2 is u (x) g1 + w (x) cof T + 2 f1 Id + f_tau d2tau with
 // u = f11 g1 + f1t cof T, w = f1t g1 + ftt cof T: two FMAs per stored entry.
+// The stored d2mu/dT2 entries of one point: reads the Jacobian A_r at
+// sA[r * ST + q], stores the NS packed entries of c_q W^-1 (d2mu/dT2) W^-T at
+// point qh of the element block He (zero at an inverted point).  ws: target
+// scale (W = ws I), iws = 1/ws, wd = ws^D, cq = w_q wd.
+template <class C, int ST, class RS, class RH, bool HAS_I2>
+__device__ __forceinline__ void hsetup_point(const ElemParams &P, const RS *sA, int q, double ws,
+                                             double iws, double wd, double cq, RH *He, int qh)
+{
+    if constexpr (std::is_same<RS, df>::value && !HAS_I2 && !std::is_same<RH, double>::value) {
+        // the factored d2mu/dT2 below, on the FP32 pipes
+        df Td[C::DD], Cd[C::DD], I1w, tauw;
+        double I1, tau;
+        point_T_dw<C::D, ST>(sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w,
+                                 &tauw);
+        if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+            for (int s = 0; s < C::NS; ++s) He[C::hoff(s, qh)] = RH(0.0f);
+            return;
+        }
+        const double sc = cq * iws * iws;
+        df a1, b1, a2, b2, dg, ft;
+        if (P.metric == MET_303 || P.metric == MET_303_55) {     // scalars in double-float too
+            InvW w;
+            metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
+            const df scw = from_db<df>(sc);
+            a1 = df(0.0f, 0.0f);                                  // f11 = 0
+            b1 = dw_mul(scw, w.f1t);
+            a2 = df(2.0f * b1.h, 2.0f * b1.l);
+            b2 = dw_mul(scw, w.ftt);
+            const df f1s = dw_mul(scw, w.f1);
+            dg = df(2.0f * f1s.h, 2.0f * f1s.l);
+            ft = dw_mul(scw, w.ft);
+        } else {
+            Inv v;
+            metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
+            a1 = from_db<df>(2.0 * sc * v.f11);
+            b1 = from_db<df>(sc * v.f1t);
+            a2 = from_db<df>(2.0 * sc * v.f1t);
+            b2 = from_db<df>(sc * v.ftt);
+            dg = from_db<df>(2.0 * sc * v.f1);
+            ft = from_db<df>(sc * v.ft);
+        }
+        df u[C::DD], w[C::DD];
+        PointStore<C, RH> ps{He, qh, RH()};
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) {
+            df x(0.0f, 0.0f), y(0.0f, 0.0f);
+            acc_add(x, a1 * Td[r]);
+            acc_add(x, b1 * Cd[r]);
+            acc_add(y, a2 * Td[r]);
+            acc_add(y, b2 * Cd[r]);
+            u[r] = norm(x);
+            w[r] = norm(y);
+            Td[r] = df(2.0f * Td[r].h, 2.0f * Td[r].l);    // g1 = 2T (exact)
+        }
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+            for (int s = r; s < C::DD; ++s) {
+                const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
+                df k(0.0f, 0.0f);
+                acc_add(k, u[r] * Td[s]);
+                acc_add(k, w[r] * Cd[s]);
+                if (r == s) acc_add(k, dprod{dg.h, dg.l});
+                if (a != cc && b != e) {
+                    if (C::D == 2) {
+                        const bool neg = (a == 0) != (b == 0);
+                        acc_add(k, neg ? dprod{-ft.h, -ft.l} : dprod{ft.h, ft.l});
+                    } else {
+                        // T = g1 / 2 at the index of the third row and column
+                        const df Tm = df(0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].h,
+                                         0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].l);
+                        const dprod pt = ft * Tm;
+                        acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
+                    }
+                }
+                ps.put(pidx<C::DD>(r, s), store_dw<RH>(norm(k)));
+            }
+        return;
+    }
+    if constexpr (std::is_same<RS, df>::value && HAS_I2 && C::D == 3 &&
+                  !std::is_same<RH, double>::value) {
+        // I2 metrics (3D): K_rs = u_r g1_s + w_r Cf_s + z_r g2_s + (2 f1 + 2 f2 I1) delta_rs
+        //   + f_tau d2tau_rs - 2 f2 (delta_ac TtT_eb + T_ae T_cb + delta_be TTt_ac),
+        // u = f11 g1 + f1t Cf + f12 g2 + 2 f2 T, w = f1t g1 + ftt Cf + f2t g2,
+        // z = f12 g1 + f2t Cf (f22 = 0), g1 = 2T: d2I2 = 4 T (x) T + 2 I1 Id - ...
+        df Td[9], Cd[9], g2w[9], TtTw[9], TTtw[9], I1w;
+        PointStore<C, RH> ps{He, qh, RH()};
+        double I1, tau;
+        point_T_dw<3, ST>(sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
+        if (!(tau > 0.0) || !(ws > 0.0)) {
+#pragma unroll
+            for (int s = 0; s < C::NS; ++s) He[C::hoff(s, qh)] = RH(0.0f);
+            return;
+        }
+        const double I2 = i2_dw(Td, Cd, I1w, g2w, TtTw, TTtw);
+        Inv v;
+        metric_scalars<3>(P.metric, I1, tau, I2, v);
+        const double sc = cq * iws * iws;
+        const df k11 = from_db<df>(2.0 * sc * v.f11), k1t = from_db<df>(sc * v.f1t);
+        const df k12 = from_db<df>(sc * v.f12), kf2 = from_db<df>(2.0 * sc * v.f2);
+        const df l1 = from_db<df>(2.0 * sc * v.f1t), ltt = from_db<df>(sc * v.ftt);
+        const df l2t = from_db<df>(sc * v.f2t), m1 = from_db<df>(2.0 * sc * v.f12);
+        const df dg = from_db<df>(2.0 * sc * (v.f1 + v.f2 * I1)), ft = from_db<df>(sc * v.ft);
+        const df m2 = from_db<df>(-2.0 * sc * v.f2);
+        df u[9], w[9], z[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            df x(0.0f, 0.0f), y(0.0f, 0.0f), zz(0.0f, 0.0f);
+            acc_add(x, k11 * Td[r]);          // f11 g1 (g1 = 2T)
+            acc_add(x, k1t * Cd[r]);
+            acc_add(x, k12 * g2w[r]);
+            acc_add(x, kf2 * Td[r]);          // 2 f2 T
+            acc_add(y, l1 * Td[r]);
+            acc_add(y, ltt * Cd[r]);
+            acc_add(y, l2t * g2w[r]);
+            acc_add(zz, m1 * Td[r]);
+            acc_add(zz, l2t * Cd[r]);
+            u[r] = norm(x);
+            w[r] = norm(y);
+            z[r] = norm(zz);
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+#pragma unroll
+            for (int s = r; s < 9; ++s) {
+                const int a = r / 3, b = r % 3, cc = s / 3, e = s % 3;
+                df k(0.0f, 0.0f);
+                acc_add(k, u[r] * df(2.0f * Td[s].h, 2.0f * Td[s].l));
+                acc_add(k, w[r] * Cd[s]);
+                acc_add(k, z[r] * g2w[s]);
+                if (r == s) acc_add(k, dprod{dg.h, dg.l});
+                if (a != cc && b != e) {
+                    const dprod pt = ft * Td[(3 - a - cc) * 3 + (3 - b - e)];
+                    acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
+                }
+                if (a == cc) acc_add(k, m2 * TtTw[e * 3 + b]);
+                acc_add(k, m2 * to_df(Td[a * 3 + e] * Td[cc * 3 + b]));
+                if (b == e) acc_add(k, m2 * TTtw[a * 3 + cc]);
+                ps.put(pidx<9>(r, s), store_dw<RH>(norm(k)));
+            }
+        return;
+    }
+    double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
+#pragma unroll
+    for (int r = 0; r < C::DD; ++r) T[r] = to_db(sA[r * ST + q]) * iws;
+    double I1, tau, I2;
+    invariants<C::D>(T, I1, tau, I2, Cf);
+    if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points store 0
+#pragma unroll
+        for (int s = 0; s < C::NS; ++s) He[C::hoff(s, qh)] = RH(0.0);
+        return;
+    }
+    Inv v;
+    metric_scalars<C::D>(P.metric, I1, tau, I2, v);
+    const double sc = cq * iws * iws;
+    PointStore<C, RH> ps{He, qh, RH()};
+    if constexpr (HAS_I2) {
+        if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+            for (int s = r; s < C::DD; ++s)
+                ps.put(pidx<C::DD>(r, s),
+                       from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v)));
+    } else {
+        double u[C::DD], w[C::DD];
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r) {
+            u[r] = sc * (v.f11 * 2.0 * T[r] + v.f1t * Cf[r]);
+            w[r] = sc * (v.f1t * 2.0 * T[r] + v.ftt * Cf[r]);
+        }
+        const double dg = 2.0 * sc * v.f1, ft = sc * v.ft;
+#pragma unroll
+        for (int r = 0; r < C::DD; ++r)
+#pragma unroll
+            for (int s = r; s < C::DD; ++s) {
+                const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
+                double k = u[r] * (2.0 * T[s]) + w[r] * Cf[s];
+                if (r == s) k += dg;
+                if (a != cc && b != e) {
+                    if (C::D == 2) k += ft * ((a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0));
+                    else k += ft * eps3(a, cc) * eps3(b, e) * T[(3 - a - cc) * 3 + (3 - b - e)];
+                }
+                ps.put(pidx<C::DD>(r, s), from_db<RH>(k));
+            }
+    }}
+
 template <class C, class RS, class RH, bool HAS_I2>
 __global__ void __launch_bounds__(C::NT)
 k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchArgs BA)
@@ -518,185 +706,7 @@ k_hsetup(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchAr
             for (int k = 1; k < C::D; ++k) wd *= ws;
         }
         const double cq = point_weight<C>(c.w, c.tx, c.ty, q3) * wd;
-        if constexpr (std::is_same<RS, df>::value && !HAS_I2 && !std::is_same<RH, double>::value) {
-            // the factored d2mu/dT2 below, on the FP32 pipes
-            df Td[C::DD], Cd[C::DD], I1w, tauw;
-            double I1, tau;
-            point_T_dw<C::D, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w,
-                                     &tauw);
-            if (!(tau > 0.0) || !(ws > 0.0)) {
-#pragma unroll
-                for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0f);
-                return;
-            }
-            const double sc = cq * iws * iws;
-            df a1, b1, a2, b2, dg, ft;
-            if (P.metric == MET_303 || P.metric == MET_303_55) {     // scalars in double-float too
-                InvW w;
-                metric303_dw(I1w, tauw, P.metric == MET_303_55, w);
-                const df scw = from_db<df>(sc);
-                a1 = df(0.0f, 0.0f);                                  // f11 = 0
-                b1 = dw_mul(scw, w.f1t);
-                a2 = df(2.0f * b1.h, 2.0f * b1.l);
-                b2 = dw_mul(scw, w.ftt);
-                const df f1s = dw_mul(scw, w.f1);
-                dg = df(2.0f * f1s.h, 2.0f * f1s.l);
-                ft = dw_mul(scw, w.ft);
-            } else {
-                Inv v;
-                metric_scalars<C::D>(P.metric, I1, tau, 0.0, v);
-                a1 = from_db<df>(2.0 * sc * v.f11);
-                b1 = from_db<df>(sc * v.f1t);
-                a2 = from_db<df>(2.0 * sc * v.f1t);
-                b2 = from_db<df>(sc * v.ftt);
-                dg = from_db<df>(2.0 * sc * v.f1);
-                ft = from_db<df>(sc * v.ft);
-            }
-            df u[C::DD], w[C::DD];
-            PointStore<C, RH> ps{He, q, RH()};
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r) {
-                df x(0.0f, 0.0f), y(0.0f, 0.0f);
-                acc_add(x, a1 * Td[r]);
-                acc_add(x, b1 * Cd[r]);
-                acc_add(y, a2 * Td[r]);
-                acc_add(y, b2 * Cd[r]);
-                u[r] = norm(x);
-                w[r] = norm(y);
-                Td[r] = df(2.0f * Td[r].h, 2.0f * Td[r].l);    // g1 = 2T (exact)
-            }
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r)
-#pragma unroll
-                for (int s = r; s < C::DD; ++s) {
-                    const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
-                    df k(0.0f, 0.0f);
-                    acc_add(k, u[r] * Td[s]);
-                    acc_add(k, w[r] * Cd[s]);
-                    if (r == s) acc_add(k, dprod{dg.h, dg.l});
-                    if (a != cc && b != e) {
-                        if (C::D == 2) {
-                            const bool neg = (a == 0) != (b == 0);
-                            acc_add(k, neg ? dprod{-ft.h, -ft.l} : dprod{ft.h, ft.l});
-                        } else {
-                            // T = g1 / 2 at the index of the third row and column
-                            const df Tm = df(0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].h,
-                                             0.5f * Td[(3 - a - cc) * 3 + (3 - b - e)].l);
-                            const dprod pt = ft * Tm;
-                            acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
-                        }
-                    }
-                    ps.put(pidx<C::DD>(r, s), store_dw<RH>(norm(k)));
-                }
-            return;
-        }
-        if constexpr (std::is_same<RS, df>::value && HAS_I2 && C::D == 3 &&
-                      !std::is_same<RH, double>::value) {
-            // I2 metrics (3D): K_rs = u_r g1_s + w_r Cf_s + z_r g2_s + (2 f1 + 2 f2 I1) delta_rs
-            //   + f_tau d2tau_rs - 2 f2 (delta_ac TtT_eb + T_ae T_cb + delta_be TTt_ac),
-            // u = f11 g1 + f1t Cf + f12 g2 + 2 f2 T, w = f1t g1 + ftt Cf + f2t g2,
-            // z = f12 g1 + f2t Cf (f22 = 0), g1 = 2T: d2I2 = 4 T (x) T + 2 I1 Id - ...
-            df Td[9], Cd[9], g2w[9], TtTw[9], TTtw[9], I1w;
-            PointStore<C, RH> ps{He, q, RH()};
-            double I1, tau;
-            point_T_dw<3, C::NQD>(c.sA, q, iws, P.target == TGT_IDENTITY, Td, Cd, I1, tau, &I1w);
-            if (!(tau > 0.0) || !(ws > 0.0)) {
-#pragma unroll
-                for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0f);
-                return;
-            }
-            const double I2 = i2_dw(Td, Cd, I1w, g2w, TtTw, TTtw);
-            Inv v;
-            metric_scalars<3>(P.metric, I1, tau, I2, v);
-            const double sc = cq * iws * iws;
-            const df k11 = from_db<df>(2.0 * sc * v.f11), k1t = from_db<df>(sc * v.f1t);
-            const df k12 = from_db<df>(sc * v.f12), kf2 = from_db<df>(2.0 * sc * v.f2);
-            const df l1 = from_db<df>(2.0 * sc * v.f1t), ltt = from_db<df>(sc * v.ftt);
-            const df l2t = from_db<df>(sc * v.f2t), m1 = from_db<df>(2.0 * sc * v.f12);
-            const df dg = from_db<df>(2.0 * sc * (v.f1 + v.f2 * I1)), ft = from_db<df>(sc * v.ft);
-            const df m2 = from_db<df>(-2.0 * sc * v.f2);
-            df u[9], w[9], z[9];
-#pragma unroll
-            for (int r = 0; r < 9; ++r) {
-                df x(0.0f, 0.0f), y(0.0f, 0.0f), zz(0.0f, 0.0f);
-                acc_add(x, k11 * Td[r]);          // f11 g1 (g1 = 2T)
-                acc_add(x, k1t * Cd[r]);
-                acc_add(x, k12 * g2w[r]);
-                acc_add(x, kf2 * Td[r]);          // 2 f2 T
-                acc_add(y, l1 * Td[r]);
-                acc_add(y, ltt * Cd[r]);
-                acc_add(y, l2t * g2w[r]);
-                acc_add(zz, m1 * Td[r]);
-                acc_add(zz, l2t * Cd[r]);
-                u[r] = norm(x);
-                w[r] = norm(y);
-                z[r] = norm(zz);
-            }
-#pragma unroll
-            for (int r = 0; r < 9; ++r)
-#pragma unroll
-                for (int s = r; s < 9; ++s) {
-                    const int a = r / 3, b = r % 3, cc = s / 3, e = s % 3;
-                    df k(0.0f, 0.0f);
-                    acc_add(k, u[r] * df(2.0f * Td[s].h, 2.0f * Td[s].l));
-                    acc_add(k, w[r] * Cd[s]);
-                    acc_add(k, z[r] * g2w[s]);
-                    if (r == s) acc_add(k, dprod{dg.h, dg.l});
-                    if (a != cc && b != e) {
-                        const dprod pt = ft * Td[(3 - a - cc) * 3 + (3 - b - e)];
-                        acc_add(k, eps3(a, cc) * eps3(b, e) > 0.0 ? pt : -pt);
-                    }
-                    if (a == cc) acc_add(k, m2 * TtTw[e * 3 + b]);
-                    acc_add(k, m2 * to_df(Td[a * 3 + e] * Td[cc * 3 + b]));
-                    if (b == e) acc_add(k, m2 * TTtw[a * 3 + cc]);
-                    ps.put(pidx<9>(r, s), store_dw<RH>(norm(k)));
-                }
-            return;
-        }
-        double T[C::DD], Cf[C::DD], g2[9], TtT[9], TTt[9];
-#pragma unroll
-        for (int r = 0; r < C::DD; ++r) T[r] = to_db(c.sA[r * C::NQD + q]) * iws;
-        double I1, tau, I2;
-        invariants<C::D>(T, I1, tau, I2, Cf);
-        if (!(tau > 0.0) || !(ws > 0.0)) {                // inverted points store 0
-#pragma unroll
-            for (int s = 0; s < C::NS; ++s) He[C::hoff(s, q)] = RH(0.0);
-            return;
-        }
-        Inv v;
-        metric_scalars<C::D>(P.metric, I1, tau, I2, v);
-        const double sc = cq * iws * iws;
-        PointStore<C, RH> ps{He, q, RH()};
-        if constexpr (HAS_I2) {
-            if (C::D == 3 && v.f2 != 0.0) dI2_3(T, I1, g2, TtT, TTt);
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r)
-#pragma unroll
-                for (int s = r; s < C::DD; ++s)
-                    ps.put(pidx<C::DD>(r, s),
-                           from_db<RH>(sc * metric_K_entry<C::D>(r, s, T, Cf, g2, TtT, TTt, I1, v)));
-        } else {
-            double u[C::DD], w[C::DD];
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r) {
-                u[r] = sc * (v.f11 * 2.0 * T[r] + v.f1t * Cf[r]);
-                w[r] = sc * (v.f1t * 2.0 * T[r] + v.ftt * Cf[r]);
-            }
-            const double dg = 2.0 * sc * v.f1, ft = sc * v.ft;
-#pragma unroll
-            for (int r = 0; r < C::DD; ++r)
-#pragma unroll
-                for (int s = r; s < C::DD; ++s) {
-                    const int a = r / C::D, b = r % C::D, cc = s / C::D, e = s % C::D;
-                    double k = u[r] * (2.0 * T[s]) + w[r] * Cf[s];
-                    if (r == s) k += dg;
-                    if (a != cc && b != e) {
-                        if (C::D == 2) k += ft * ((a == 0 ? 1.0 : -1.0) * (b == 0 ? 1.0 : -1.0));
-                        else k += ft * eps3(a, cc) * eps3(b, e) * T[(3 - a - cc) * 3 + (3 - b - e)];
-                    }
-                    ps.put(pidx<C::DD>(r, s), from_db<RH>(k));
-                }
-        }
+        hsetup_point<C, C::NQD, RS, RH, HAS_I2>(P, c.sA, q, ws, iws, wd, cq, He, q);
     });
 }
 

@@ -45,63 +45,22 @@ struct Grad3cShape {
         sizeof(df) * (size_t)(TAB + 9 * C::NQ * S::NT + 3 * C::NQ * S::NT);
 };
 
-template <class C, int MINB>
-__global__ void __launch_bounds__(128, MINB)
-k_grad3c(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, double *part,
-         BatchArgs BA, const GradTab<df, C::NI, C::NQ> T)
+// Forward pass of the warp-synchronous geometry kernels: the Jacobian A_{c b}
+// at the points of element e into the warp's columns cs [(3 c + b) NQ + q3]
+// and the physical point coordinates into xs [c NQ + q3] (32-lane stride), by
+// B/G sum factorisation of the positions minus the element's first node, with
+// every partial sum renormalised; fu, fb, fg: the element's buffers (in column
+// rows 6-8, dead until component 2 is stored).
+template <class C>
+__device__ __forceinline__ void grad3c_forward(const ElemParams &P, const double *__restrict__ x,
+                                               int64_t e, bool valid, int t, int tx, int ty,
+                                               int lane, const int *m, int m0, const df *Bs,
+                                               const df *Gs, const GradTab<df, C::NI, C::NQ> &T,
+                                               df *cs, df *xs, df *fu, df *fb, df *fg)
 {
-    static_assert(C::D == 3, "3D kernel");
     using S = Apply3cShape<C, 4>;
     using RC = df;
-    static_assert(S::NT == C::NT && S::EPB == C::EPB, "the CTA is one element tile");
     constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP;
-
-    // part != nullptr (or a batch aux role): also the energy and min det partials
-    const void *in = x, *aux = part;
-    void *out = ev;
-    const int *stop = nullptr;
-    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
-    x = static_cast<const double *>(in);
-    ev = static_cast<double *>(out);
-    part = const_cast<double *>(static_cast<const double *>(aux));
-
-    using G3 = Grad3cShape<C>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    RC *Bs = reinterpret_cast<RC *>(smem);                  // B[q * NI + i]
-    RC *Gs = Bs + NQ * NI;                                  // G[q * NI + i]
-    if (threadIdx.x == 0) {                                 // compile-time indices only
-#pragma unroll
-        for (int i = 0; i < NQ * NI; ++i) Bs[i] = T.B[i];
-#pragma unroll
-        for (int i = 0; i < NQ * NI; ++i) Gs[i] = T.G[i];
-    }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = lane / S::TPE;
-    const bool act = slot < S::EPW;
-    const int t = lane - slot * S::TPE;
-    const int tx = t % NQ, ty = t / NQ;
-    const int64_t e = tile * C::EPB + warp * S::EPW + (act ? slot : 0);
-    const bool valid = act && e < P.E;
-    // the warp's columns [(r * NQ + q3) * 32 + lane]: Jacobian then integrand
-    // rows r = 3 c + b, and the physical point coordinates (size target)
-    RC *cs = Bs + G3::TAB + warp * 9 * NQ * 32;
-    RC *xs = Bs + G3::TAB + 9 * NQ * S::NT + warp * 3 * NQ * 32;
-    // forward buffers in rows 6-8: nodes u, B1 u, G1 u [(i3 * NI + i2) * NQ + q1]
-    RC *fu = cs + 6 * NQ * 32 + (act ? slot : 0) * G3::FB;
-    RC *fb = fu + NP;
-    RC *fg = fb + NI * NI * NQ;
-    int m[S::NPL];
-#pragma unroll
-    for (int j = 0; j < S::NPL; ++j) {
-        const int i = t + j * S::TPE;
-        m[j] = (valid && i < NP) ? P.map[e * NP + i] : 0;
-    }
-    const int m0 = valid ? P.map[e * NP] : 0;              // the element's first node
-
-    // ---- forward: A_{c b} at the points (element-local positions), B and G,
-    // every partial sum renormalised (the accuracy of A bounds that of dmu/dT)
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         const double off = valid ? x[c * P.Nx + m0] : 0.0;
@@ -188,6 +147,65 @@ k_grad3c(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, do
         }
         __syncwarp();                                       // the buffers are reused by the next gather
     }
+
+}
+
+template <class C, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_grad3c(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, double *part,
+         BatchArgs BA, const GradTab<df, C::NI, C::NQ> T)
+{
+    static_assert(C::D == 3, "3D kernel");
+    using S = Apply3cShape<C, 4>;
+    using RC = df;
+    static_assert(S::NT == C::NT && S::EPB == C::EPB, "the CTA is one element tile");
+    constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP;
+
+    // part != nullptr (or a batch aux role): also the energy and min det partials
+    const void *in = x, *aux = part;
+    void *out = ev;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    x = static_cast<const double *>(in);
+    ev = static_cast<double *>(out);
+    part = const_cast<double *>(static_cast<const double *>(aux));
+
+    using G3 = Grad3cShape<C>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    RC *Bs = reinterpret_cast<RC *>(smem);                  // B[q * NI + i]
+    RC *Gs = Bs + NQ * NI;                                  // G[q * NI + i]
+    if (threadIdx.x == 0) {                                 // compile-time indices only
+#pragma unroll
+        for (int i = 0; i < NQ * NI; ++i) Bs[i] = T.B[i];
+#pragma unroll
+        for (int i = 0; i < NQ * NI; ++i) Gs[i] = T.G[i];
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = lane / S::TPE;
+    const bool act = slot < S::EPW;
+    const int t = lane - slot * S::TPE;
+    const int tx = t % NQ, ty = t / NQ;
+    const int64_t e = tile * C::EPB + warp * S::EPW + (act ? slot : 0);
+    const bool valid = act && e < P.E;
+    // the warp's columns [(r * NQ + q3) * 32 + lane]: Jacobian then integrand
+    // rows r = 3 c + b, and the physical point coordinates (size target)
+    RC *cs = Bs + G3::TAB + warp * 9 * NQ * 32;
+    RC *xs = Bs + G3::TAB + 9 * NQ * S::NT + warp * 3 * NQ * 32;
+    // forward buffers in rows 6-8: nodes u, B1 u, G1 u [(i3 * NI + i2) * NQ + q1]
+    RC *fu = cs + 6 * NQ * 32 + (act ? slot : 0) * G3::FB;
+    RC *fb = fu + NP;
+    RC *fg = fb + NI * NI * NQ;
+    int m[S::NPL];
+#pragma unroll
+    for (int j = 0; j < S::NPL; ++j) {
+        const int i = t + j * S::TPE;
+        m[j] = (valid && i < NP) ? P.map[e * NP + i] : 0;
+    }
+    const int m0 = valid ? P.map[e * NP] : 0;              // the element's first node
+
+    grad3c_forward<C>(P, x, e, valid, t, tx, ty, lane, m, m0, Bs, Gs, T, cs, xs, fu, fb, fg);
 
     // ---- pointwise: the integrand c_q dmu/dT W^-T over the Jacobian columns
     double esum = 0.0, emin = INFINITY;
@@ -296,6 +314,82 @@ k_grad3c(ElemParams P, const double *__restrict__ x, double *__restrict__ ev, do
             }
         }
         __syncwarp();                                       // the buffers are reused by the next component
+    }
+}
+
+
+// Partial-assembly set-up on the same forward pass: the stored d2mu/dT2 entries
+// of every point (hsetup_point, shared with the block kernel k_hsetup), each
+// lane storing its own points (entry pairs: one 8- or 16-byte store per two
+// entries across consecutive lanes).  Paper Sec. 3.4.
+template <class C, class RH, bool HAS_I2, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_hset3c(ElemParams P, const double *__restrict__ x, RH *__restrict__ H, BatchArgs BA,
+         const GradTab<df, C::NI, C::NQ> T)
+{
+    static_assert(C::D == 3, "3D kernel");
+    using S = Apply3cShape<C, 4>;
+    using RC = df;
+    static_assert(S::NT == C::NT && S::EPB == C::EPB, "the CTA is one element tile");
+    constexpr int NI = C::NI, NQ = C::NQ, NP = C::NP;
+
+    const void *in = x, *aux = nullptr;
+    void *out = H;
+    const int *stop = nullptr;
+    const int64_t tile = resolve_tile(P, BA, in, aux, out, stop);
+    x = static_cast<const double *>(in);
+    H = static_cast<RH *>(out);
+
+    using G3 = Grad3cShape<C>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    RC *Bs = reinterpret_cast<RC *>(smem);                  // B[q * NI + i]
+    RC *Gs = Bs + NQ * NI;                                  // G[q * NI + i]
+    if (threadIdx.x == 0) {                                 // compile-time indices only
+#pragma unroll
+        for (int i = 0; i < NQ * NI; ++i) Bs[i] = T.B[i];
+#pragma unroll
+        for (int i = 0; i < NQ * NI; ++i) Gs[i] = T.G[i];
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = lane / S::TPE;
+    const bool act = slot < S::EPW;
+    const int t = lane - slot * S::TPE;
+    const int tx = t % NQ, ty = t / NQ;
+    const int64_t e = tile * C::EPB + warp * S::EPW + (act ? slot : 0);
+    const bool valid = act && e < P.E;
+    RC *cs = Bs + G3::TAB + warp * 9 * NQ * 32;
+    RC *xs = Bs + G3::TAB + 9 * NQ * S::NT + warp * 3 * NQ * 32;
+    RC *fu = cs + 6 * NQ * 32 + (act ? slot : 0) * G3::FB;
+    RC *fb = fu + NP;
+    RC *fg = fb + NI * NI * NQ;
+    int m[S::NPL];
+#pragma unroll
+    for (int j = 0; j < S::NPL; ++j) {
+        const int i = t + j * S::TPE;
+        m[j] = (valid && i < NP) ? P.map[e * NP + i] : 0;
+    }
+    const int m0 = valid ? P.map[e * NP] : 0;
+    grad3c_forward<C>(P, x, e, valid, t, tx, ty, lane, m, m0, Bs, Gs, T, cs, xs, fu, fb, fg);
+    if (!valid) return;                                     // no barrier follows
+
+    RH *He = H + e * (int64_t)C::HST;
+    const int pt = ty * NQ + tx;
+#pragma unroll 1
+    for (int q3 = 0; q3 < NQ; ++q3) {
+        double ws = 1.0, iws = 1.0, wd = 1.0;               // identity target: W = I
+        if (P.target != TGT_IDENTITY) {
+            double xq[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xq[k] = to_db(xs[(k * NQ + q3) * 32 + lane]);
+            ws = target_scale<3>(P.target, P.h0, xq);
+            iws = 1.0 / ws;
+            wd = ws * ws * ws;
+        }
+        const double cq = to_db(T.w[tx]) * to_db(T.w[ty]) * to_db(T.w[q3]) * wd;
+        hsetup_point<C, NQ * 32, RC, RH, HAS_I2>(P, cs + lane, q3 * 32, ws, iws, wd, cq, He,
+                                                 q3 * NQ * NQ + pt);
     }
 }
 
