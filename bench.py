@@ -40,7 +40,7 @@ MINRES_ITS = 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one action launch, captured on the
 # 24^3 Q3 case and scaled by elements (x8) to a 48^3 launch; None when the kernel changed
 # since the capture.
-TRAFFIC_BYTES = {("fp64", 13): 2.691e9, ("fp32", 17): 1.366e9}     # (precision, action variant)
+TRAFFIC_BYTES = {("fp64", 13): 2.692e9, ("fp32", 17): 1.367e9}     # (precision, action variant)
 PRECISION_LABEL = {"fp64": "fp64-class (double-float contractions, 48-bit significand)",
                    "fp32": "fp32-mixed (fp32 stored d2mu/dT2, action and MINRES; fp64 residual, "
                            "energy, det and line search)",
