@@ -179,16 +179,16 @@ __global__ void b_minres_init(const BMesh *M, const int2 *tiles, int r1, int r2,
     const R *mi = rp<R>(bm, ROLE_MINV);
     R *R1 = rp<R>(bm, ROLE_KV0 + r1), *R2 = rp<R>(bm, ROLE_KV0 + r2), *Y = rp<R>(bm, ROLE_KV0 + y);
     __shared__ double sh[BT / 32];
-    double s = 0.0;
+    VecDot<R> dot;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
         const R bi = (R)b[i];
         const R yi = mi[i] * bi;
         R1[i] = bi;
         R2[i] = bi;
         Y[i] = yi;
-        s += (double)bi * (double)yi;
+        dot.add(bi, yi);
     }
-    s = bsum(s, sh);
+    const double s = bsum(dot.get(), sh);
     if (threadIdx.x == 0) rp<double>(bm, ROLE_VPART)[t.y] = s;
 }
 
@@ -215,8 +215,8 @@ __global__ void b_minres_scale(const BMesh *M, const int2 *tiles, const BState *
     chunk_range(bm, t.y, i0, i1);
     const R *Y = rp<R>(bm, ROLE_KV0 + y);
     R *V = rp<R>(bm, ROLE_KV0 + v);
-    const double ib = 1.0 / ms.beta;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) V[i] = (R)((double)Y[i] * ib);
+    const VecS<R> ib = (VecS<R>)(1.0 / ms.beta);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) V[i] = (R)((VecS<R>)Y[i] * ib);
 }
 
 template <class R>
@@ -232,15 +232,16 @@ __global__ void b_lanczos_a(const BMesh *M, const int2 *tiles, const BState *S, 
     chunk_range(bm, t.y, i0, i1);
     R *Z = rp<R>(bm, ROLE_KV0 + z);
     const R *R1 = rp<R>(bm, ROLE_KV0 + r1), *V = rp<R>(bm, ROLE_KV0 + v);
-    const double c = (k >= 2) ? ms.beta / ms.beta_old : 0.0;
+    using SR = VecS<R>;
+    const SR c = (SR)((k >= 2) ? ms.beta / ms.beta_old : 0.0);
     __shared__ double sh[BT / 32];
-    double s = 0.0;
+    VecDot<R> dot;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
-        const R yi = (R)((double)Z[i] - c * (double)R1[i]);
+        const R yi = (R)((SR)Z[i] - c * (SR)R1[i]);
         Z[i] = yi;
-        s += (double)V[i] * (double)yi;
+        dot.add(V[i], yi);
     }
-    s = bsum(s, sh);
+    const double s = bsum(dot.get(), sh);
     if (threadIdx.x == 0) rp<double>(bm, ROLE_VPART)[t.y] = s;
 }
 
@@ -271,17 +272,18 @@ __global__ void b_lanczos_b(const BMesh *M, const int2 *tiles, const BState *S, 
     chunk_range(bm, t.y, i0, i1);
     R *Y = rp<R>(bm, ROLE_KV0 + y), *YN = rp<R>(bm, ROLE_KV0 + ynew);
     const R *R2 = rp<R>(bm, ROLE_KV0 + r2), *mi = rp<R>(bm, ROLE_MINV);
-    const double c = ms.alpha / ms.beta;
+    using SR = VecS<R>;
+    const SR c = (SR)(ms.alpha / ms.beta);
     __shared__ double sh[BT / 32];
-    double s = 0.0;
+    VecDot<R> dot;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
-        const R yi = (R)((double)Y[i] - c * (double)R2[i]);
+        const R yi = (R)((SR)Y[i] - c * (SR)R2[i]);
         const R zi = mi[i] * yi;
         Y[i] = yi;
         YN[i] = zi;
-        s += (double)yi * (double)zi;
+        dot.add(yi, zi);
     }
-    s = bsum(s, sh);
+    const double s = bsum(dot.get(), sh);
     if (threadIdx.x == 0) rp<double>(bm, ROLE_VPART)[t.y] = s;
 }
 
@@ -315,13 +317,15 @@ __global__ void b_minres_update(const BMesh *M, const int2 *tiles, const BState 
     const R *W1 = rp<R>(bm, ROLE_KV0 + w1), *W2 = rp<R>(bm, ROLE_KV0 + w2);
     const R *YN = rp<R>(bm, ROLE_KV0 + ynew);
     double *dx = rp<double>(bm, ROLE_DX);
-    const double eo = ms.eps_old, de = ms.delta, ig = 1.0 / ms.gamma, ph = ms.phi;
-    const double ib = (ms.beta > 0.0) ? 1.0 / ms.beta : 0.0;
+    using SR = VecS<R>;
+    const SR eo = (SR)ms.eps_old, de = (SR)ms.delta, ig = (SR)(1.0 / ms.gamma);
+    const double ph = ms.phi;
+    const SR ib = (SR)((ms.beta > 0.0) ? 1.0 / ms.beta : 0.0);
     for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
-        const double wn = ((double)V[i] - eo * (double)W1[i] - de * (double)W2[i]) * ig;
+        const SR wn = ((SR)V[i] - eo * (SR)W1[i] - de * (SR)W2[i]) * ig;
         WN[i] = (R)wn;
-        dx[i] += ph * wn;
-        V[i] = (R)((double)YN[i] * ib);
+        dx[i] += ph * (double)wn;                           // the solution stays FP64
+        V[i] = (R)((SR)YN[i] * ib);
     }
 }
 

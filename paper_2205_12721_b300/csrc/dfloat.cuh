@@ -303,4 +303,28 @@ __device__ __forceinline__ void ev_accum(RV *p, const RC &a)
     }
 }
 
+// Per-DOF arithmetic of the MINRES vector kernels in the type S of the
+// vectors' updates: double for FP64 vectors; float for FP32 vectors (the
+// vectors are FP32 already; the float <-> double conversions and FP64 adds of
+// a double evaluation ran on B300's FP64 pipe and bounded these kernels).
+template <class R> using VecS = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+
+// Dot-product partial sums: double for FP64 vectors; for FP32 vectors the
+// exact float products summed in double-float on the FP32 pipes (TwoProd and
+// TwoSum), converted to double once per thread.
+template <class R> struct VecDot {
+    double s = 0.0;
+    __device__ __forceinline__ void add(R a, R b) { s += (double)a * (double)b; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct VecDot<float> {
+    df s = df(0.0f, 0.0f);
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        acc_add(s, dprod{p, fmaf(a, b, -p)});
+    }
+    __device__ __forceinline__ double get() const { return (double)s.h + (double)s.l; }
+};
+
 }  // namespace tmop

@@ -32,6 +32,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;   // valid on thread 0
 }
 
+
 // y[dof] = sum over the element entries of the node (fixed order), then the
 // fixed-DOF rule: mode 0 -> 0, mode 1 -> vfix[dof] (or 0), mode 2 -> 1.
 template <class RI, class RO>
@@ -141,16 +142,17 @@ __global__ void k_minres_init(const double *__restrict__ b, const R *__restrict_
                               double *__restrict__ part)
 {
     __shared__ double sh[VT / 32];
-    double s = 0.0;
+    double s;
+    VecDot<R> dot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const R bi = (R)b[i];
         const R yi = minv[i] * bi;
         r1[i] = bi;
         r2[i] = bi;
         y[i] = yi;
-        s += (double)bi * (double)yi;
+        dot.add(bi, yi);
     }
-    s = block_sum(s, sh);
+    s = block_sum(dot.get(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -169,9 +171,9 @@ __global__ void k_minres_scale(const R *__restrict__ y, const MinresState *__res
                                R *__restrict__ v)
 {
     if (st->stop_iter < 1) return;
-    const double ib = 1.0 / st->beta;
+    const VecS<R> ib = (VecS<R>)(1.0 / st->beta);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = (R)((double)y[i] * ib);
+        v[i] = (R)((VecS<R>)y[i] * ib);
 }
 
 // y = z - (beta/beta_old) r1 (k >= 2), in place in z; partial dot(v, y).
@@ -183,14 +185,15 @@ __global__ void k_lanczos_a(R *__restrict__ z, const R *__restrict__ r1, const R
     if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
-    const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
-    double s = 0.0;
+    using S = VecS<R>;
+    const S c = (S)((k >= 2) ? st->beta / st->beta_old : 0.0);
+    VecDot<R> dot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R yi = (R)((double)z[i] - c * (double)r1[i]);
+        const R yi = (R)((S)z[i] - c * (S)r1[i]);
         z[i] = yi;
-        s += (double)v[i] * (double)yi;
+        dot.add(v[i], yi);
     }
-    s = block_sum(s, sh);
+    const double s = block_sum(dot.get(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -208,8 +211,9 @@ __global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *_
     if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
-    const double c = (k >= 2) ? st->beta / st->beta_old : 0.0;
-    double dsum = 0.0;
+    using S = VecS<R>;
+    const S c = (S)((k >= 2) ? st->beta / st->beta_old : 0.0);
+    VecDot<R> dot;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < Nx; n += (int64_t)gridDim.x * blockDim.x) {
         const int b = ptr[n], e = ptr[n + 1];
         typename AsmAcc<RI>::T s[3];
@@ -229,12 +233,12 @@ __global__ void k_assemble_lanczos_a(const RI *__restrict__ ev, const int32_t *_
             if (a >= D) break;
             const int64_t dof = a * Nx + n;
             const R z = (fixed && fixed[dof]) ? R(0) : asm_out<R>(s[a]);
-            const R yi = (R)((double)z - c * (double)r1[dof]);
+            const R yi = (R)((S)z - c * (S)r1[dof]);
             y[dof] = yi;
-            dsum += (double)v[dof] * (double)yi;
+            dot.add(v[dof], yi);
         }
     }
-    dsum = block_sum(dsum, sh);
+    const double dsum = block_sum(dot.get(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = dsum;
 }
 
@@ -260,16 +264,17 @@ __global__ void k_lanczos_b(R *__restrict__ y, const R *__restrict__ r2, const R
     if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
     __shared__ double sh[VT / 32];
-    const double c = st->alpha / st->beta;
-    double s = 0.0;
+    using S = VecS<R>;
+    const S c = (S)(st->alpha / st->beta);
+    VecDot<R> dot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R yi = (R)((double)y[i] - c * (double)r2[i]);
+        const R yi = (R)((S)y[i] - c * (S)r2[i]);
         const R zi = minv[i] * yi;
         y[i] = yi;
         ynew[i] = zi;
-        s += (double)yi * (double)zi;
+        dot.add(yi, zi);
     }
-    s = block_sum(s, sh);
+    const double s = block_sum(dot.get(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -295,13 +300,15 @@ __global__ void k_minres_update(R *__restrict__ v, const R *__restrict__ w1, con
 {
     if (k < 0) k = st->k;                                  // device iteration counter
     if (st->stop_iter < k) return;
-    const double eo = st->eps_old, de = st->delta, ig = 1.0 / st->gamma, ph = st->phi;
-    const double ib = (st->beta > 0.0) ? 1.0 / st->beta : 0.0;
+    using S = VecS<R>;
+    const S eo = (S)st->eps_old, de = (S)st->delta, ig = (S)(1.0 / st->gamma);
+    const double ph = st->phi;
+    const S ib = (S)((st->beta > 0.0) ? 1.0 / st->beta : 0.0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double wn = ((double)v[i] - eo * (double)w1[i] - de * (double)w2[i]) * ig;
+        const S wn = ((S)v[i] - eo * (S)w1[i] - de * (S)w2[i]) * ig;
         wnew[i] = (R)wn;
-        dx[i] += ph * wn;
-        v[i] = (R)((double)ynew[i] * ib);
+        dx[i] += ph * (double)wn;                           // the solution stays FP64
+        v[i] = (R)((S)ynew[i] * ib);
     }
 }
 
