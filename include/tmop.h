@@ -190,9 +190,19 @@ tmop_status tmop_hessian_diag(tmop_ctx *ctx, void *diag);
  * Synchronises.  Returns TMOP_ERR_INVERTED if x is inverted,
  * TMOP_ERR_LINESEARCH if no step length passed (x unchanged),
  * TMOP_ERR_MINRES on breakdown.  A stationary x (dF = 0) returns TMOP_OK
- * with alpha = 0. */
+ * with alpha = 0.  The energy, min det and gradient the line search computed
+ * at the accepted positions are kept with a copy of them: the next step
+ * takes them instead of evaluating again when its x is bitwise equal to
+ * that copy (one compare pass over x) and no call that changes the energy
+ * (tmop_set_limit_reference, tmop_set_target_field, tmop_set_remap_source)
+ * came in between; steps with a remap source always evaluate.  The same
+ * kernels on the same input give the same bits, so results do not depend on
+ * the reuse. */
 tmop_status tmop_newton_step(tmop_ctx *ctx, double *x, const tmop_solver_opts *opts,
                              tmop_step_report *rep);
+/* Number of Newton steps of this context that reused the evaluation at the
+ * previous step's accepted positions (diagnostics). */
+int64_t tmop_step_reuses(const tmop_ctx *ctx);
 
 /* det(A) at every quadrature point of the mesh x (Sec. 2.2, eq. A:
  * A = sum_i x_{E,i} grad(w_i)^T, the Jacobian of the reference-to-physical

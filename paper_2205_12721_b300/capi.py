@@ -27,7 +27,7 @@ K_REMAP_SETUP, K_MASS, K_ADVECT = 7, 8, 9
 EXPORTS = ("tmop_setup", "tmop_energy", "tmop_gradient", "tmop_hessian_setup",
            "tmop_hessian_apply", "tmop_hessian_diag", "tmop_newton_step", "tmop_destroy",
            "tmop_status_string", "tmop_last_error", "tmop_launch_count", "tmop_profile_enable",
-           "tmop_set_graphs", "tmop_graph_launches",
+           "tmop_set_graphs", "tmop_graph_launches", "tmop_step_reuses",
            "tmop_profile_read", "tmop_device_bytes", "tmop_energy_noalloc",
            "tmop_batch_create", "tmop_batch_add", "tmop_batch_step", "tmop_batch_state",
            "tmop_batch_positions", "tmop_batch_remove", "tmop_batch_mesh_bytes",
@@ -144,6 +144,7 @@ def lib():
             "tmop_profile_enable": (I, [P, I]),
             "tmop_set_graphs": (I, [P, I]),
             "tmop_graph_launches": (I64, [P]),
+            "tmop_step_reuses": (I64, [P]),
             "tmop_profile_read": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]),
             "tmop_device_bytes": (I64, [P]),
             "tmop_energy_noalloc": (I, [ctypes.POINTER(Desc), P, P, P, P]),
@@ -366,6 +367,10 @@ def tmop_set_graphs(ctx: int, on: bool = True):
 
 def tmop_graph_launches(ctx: int) -> int:
     return int(lib().tmop_graph_launches(ctx))
+
+
+def tmop_step_reuses(ctx: int) -> int:
+    return int(lib().tmop_step_reuses(ctx))
 
 
 def tmop_profile_read(ctx: int, kernel_class: int):

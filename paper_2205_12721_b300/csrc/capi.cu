@@ -96,6 +96,12 @@ struct tmop_ctx {
     double *hscal = nullptr;     // pinned host mirror
     // Newton / MINRES work
     double *g = nullptr, *dx = nullptr, *xt = nullptr;
+    // F, min det and |g| at the positions the last Newton step accepted (kept
+    // in xt, the gradient in g): the next step reuses them when its x equals
+    // xt bitwise and nothing that defines the energy changed in between
+    bool fg_valid = false;
+    double fg_F = 0.0, fg_md = 0.0, fg_gn = 0.0;
+    int64_t reused_fg = 0;             // steps that took them (tmop_step_reuses)
     void *vm = nullptr, *diagR = nullptr, *minv = nullptr;
     void *kv[8] = {nullptr};     // v, R1, R2, Z, W1, W2, W3, spare
     MinresState *st = nullptr, *hst = nullptr;
@@ -957,13 +963,33 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         st = remap_run(c, c->rsrc_x0, x, c->rsrc_eta0, c->eta, c->remap_opts, nullptr);
         if (st != TMOP_OK) return finish(st);
     }
-    st = energy_grad_sync(c, x, c->g, &F0, &md0);
-    r.energy = F0;
-    r.min_det = md0;
-    if (st != TMOP_OK) return finish(st);
+    // F, min det and g at x: those of the previous step's accepted trial when
+    // x is still those positions (the same kernels on the same input give
+    // the same bits), else evaluated
+    bool reuse = false;
+    if (c->fg_valid && !c->remap_on) {
+        CK(launch_differs(x, c->xt, c->ndof, c->scal + 7, c->stream));
+        CK(cudaMemcpyAsync(c->hscal + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        reuse = c->hscal[7] == 0.0;
+    }
+    c->fg_valid = false;
     double g0 = 0;
-    st = norm_sync(c, c->g, &g0);
-    if (st != TMOP_OK) return finish(st);
+    if (reuse) {
+        F0 = c->fg_F;
+        md0 = c->fg_md;
+        g0 = c->fg_gn;
+        r.energy = F0;
+        r.min_det = md0;
+        c->reused_fg += 1;
+    } else {
+        st = energy_grad_sync(c, x, c->g, &F0, &md0);
+        r.energy = F0;
+        r.min_det = md0;
+        if (st != TMOP_OK) return finish(st);
+        st = norm_sync(c, c->g, &g0);
+        if (st != TMOP_OK) return finish(st);
+    }
     r.grad_norm = g0;
     if (g0 == 0.0) {
         r.energy_new = F0;
@@ -1021,6 +1047,10 @@ tmop_status tmop_newton_step(tmop_ctx *c, double *x, const tmop_solver_opts *opt
         r.energy_new = F1;
         r.grad_norm_new = g1;
         r.min_det = md1;
+        c->fg_valid = true;                                     // xt = x, g at xt
+        c->fg_F = F1;
+        c->fg_md = md1;
+        c->fg_gn = g1;
         g_last_error.clear();
         return finish(TMOP_OK);
     }
@@ -1033,6 +1063,7 @@ tmop_status tmop_set_limit_reference(tmop_ctx *ctx, const double *x0)
     if (ctx->lim2 <= 0.0) return fail(TMOP_ERR_ARG, "context has no limiting term (limit_delta = 0)");
     CK(cudaMemcpyAsync(ctx->x0, x0, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->x0_set = true;
+    ctx->fg_valid = false;
     return TMOP_OK;
 }
 
@@ -1043,6 +1074,7 @@ tmop_status tmop_set_target_field(tmop_ctx *ctx, const double *eta)
     TRY(eta_alloc(ctx));
     CK(cudaMemcpyAsync(ctx->eta, eta, sizeof(double) * ctx->Nx, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->eta_set = true;
+    ctx->fg_valid = false;
     return TMOP_OK;
 }
 
@@ -1051,6 +1083,7 @@ tmop_status tmop_set_remap_source(tmop_ctx *ctx, const double *x0, const double 
 {
     if (!ctx) return fail(TMOP_ERR_ARG, "NULL context");
     if (ctx->desc.target != TMOP_TARGET_DISCRETE) return fail(TMOP_ERR_ARG, "context target is not DISCRETE");
+    ctx->fg_valid = false;
     if (!eta0) {
         ctx->remap_on = false;
         return TMOP_OK;
@@ -1091,6 +1124,7 @@ tmop_status tmop_set_graphs(tmop_ctx *ctx, int on)
 }
 
 int64_t tmop_graph_launches(const tmop_ctx *ctx) { return ctx ? ctx->graph_launches : 0; }
+int64_t tmop_step_reuses(const tmop_ctx *ctx) { return ctx ? ctx->reused_fg : 0; }
 
 tmop_status tmop_profile_enable(tmop_ctx *ctx, int on)
 {

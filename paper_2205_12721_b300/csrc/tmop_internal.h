@@ -127,6 +127,8 @@ cudaError_t launch_mask(const void *v, const uint8_t *fixed, int64_t n, void *ou
                         cudaStream_t s);
 cudaError_t launch_trial(const double *x, const double *dx, double alpha, int64_t n, double *out,
                          cudaStream_t s);
+// *flag (device) = 1.0 when a and b differ bitwise in some entry, else 0.0.
+cudaError_t launch_differs(const double *a, const double *b, int64_t n, double *flag, cudaStream_t s);
 cudaError_t launch_dot(const void *a, const void *b, int prec, int64_t n, double *part, int nb,
                        cudaStream_t s);
 cudaError_t launch_dot_masked(const double *a, const double *b, const uint8_t *mask, int64_t n,

@@ -83,6 +83,17 @@ __global__ void k_trial(const double *__restrict__ x, const double *__restrict__
         out[i] = x[i] - alpha * dx[i];
 }
 
+// *flag = 1 when a and b differ in any bit of any entry (left untouched
+// otherwise); every writer stores the same value.
+__global__ void k_differs(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                          double *__restrict__ flag)
+{
+    bool d = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d |= __double_as_longlong(a[i]) != __double_as_longlong(b[i]);
+    if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) *flag = 1.0;
+}
+
 template <class R>
 __global__ void k_dot(const R *__restrict__ a, const R *__restrict__ b, int64_t n,
                       double *__restrict__ part)
@@ -627,6 +638,15 @@ cudaError_t launch_trial(const double *x, const double *dx, double alpha, int64_
 {
     if (n == 0) return cudaSuccess;
     k_trial<<<grid_for(n), VT, 0, s>>>(x, dx, alpha, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_differs(const double *a, const double *b, int64_t n, double *flag, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(double), s);
+    if (e != cudaSuccess || n == 0) return e;
+    k_differs<<<grid_for(n), VT, 0, s>>>(a, b, n, flag);
     count_launch();
     return cudaGetLastError();
 }
